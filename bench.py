@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Throughput of the gradient-residual evaluation (forward John transform +
+SH contraction + weighted residual + back-contraction + exact adjoint) on one
+GB300, through libtt's C ABI.
+
+Workload (one step = one gradient evaluation): 64^3 voxels, l_max = 4
+(K = 15), 120 projections (20 rotations 18 deg apart x 6 tilts 0..45 deg) of
+64 x 64 pixels x 16 segments over [0, 180 deg), 6-ellipsoid fibre phantom,
+Poisson data at mean 1e4, weights all ones, FP32.  Inputs are synthetic and
+resident in HBM; L2 is flushed (512 MB write) between timed steps.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores instead.  With torchrun (N > 1) each rank runs an independent
+replica (the evaluation is single-GPU; there is no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gradient evals/s (fwd+adjoint SH projector), % HBM roofline; time-to-loss vs plain"
+UNIT = "evals/s"
+WORKLOAD = "ell64"
+WORKLOAD_DESC = ("ell64: 64^3 voxels, l_max 4 (K=15), 120 projections (20 rotations x 6 tilts 0-45 deg) "
+                 "of 64x64 pixels x 16 segments, 6-ellipsoid fibre phantom (seed 1), Poisson counts at mean 1e4, "
+                 "W = 1, FP32")
+FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-evals", type=float, default=2.0,
+                    help="oracle sample size in full-workload gradient evaluations")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2504_16446_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch for a kernel from the committed ncu summary, or
+    None if the kernel sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        if t.get("source_hash") != _kernel_source_hash():
+            return None
+        return t["kernels"][kernel]["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_rate(st, c, I, W, sample_evals: float):
+    """Oracle (FP64 C, single thread) gradient evaluations per second on a
+    bounded sample: whole-workload evaluations repeated, or a projection
+    subset for fractional sample sizes, scaled to the full workload."""
+    import numpy as np
+    import oracle
+    S = st.S
+    n_proj = max(1, min(S, int(round(S * min(1.0, sample_evals)))))
+    reps = max(1, int(round(sample_evals))) if sample_evals >= 1.0 else 1
+    proj = np.linspace(0, S - 1, n_proj).round().astype(int)
+    sub = st.subset(proj)
+    g = oracle.Geometry(sub.shape, sub.nj, sub.nk, sub.ell_max, sub.inner_angle, sub.outer_angle,
+                        sub.seg_start, sub.seg_end, j_offset=sub.j_offset, k_offset=sub.k_offset,
+                        two_theta=sub.two_theta, a=sub.a, b=sub.b)
+    B = oracle.basis_matrix(g)
+    c64 = np.asarray(c, dtype=np.float64)
+    I64 = np.ascontiguousarray(np.asarray(I, dtype=np.float64)[proj])
+    W64 = None if W is None else np.ascontiguousarray(np.asarray(W, dtype=np.float64)[proj])
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.gradient_residual(g, c64, I64, W64, B)
+    dt = time.perf_counter() - t0
+    evals = reps * n_proj / S
+    return evals / dt, dt, f"{reps} x gradient evaluation over {n_proj}/{S} projections ({evals:.3g} full evals, {dt:.1f} s)"
+
+
+def make_inputs(st, torch, tt, synth):
+    """Phantom -> SH coefficients (GPU kernel) -> data by the GPU forward
+    projection with Poisson noise (counts at mean 1e4, rescaled)."""
+    ph = synth.phantom(WORKLOAD)
+    dirs = torch.as_tensor(ph.dirs.reshape(-1, 3), dtype=torch.float32, device="cuda")
+    amps = torch.as_tensor(ph.amps.reshape(-1, st.ell_max // 2 + 1), dtype=torch.float32, device="cuda")
+    c_true = tt.zonal_to_sh(st.ell_max, dirs, amps).reshape(st.volume_shape).contiguous()
+    h = tt.Handle(st, "f32")
+    clean = h.project(c_true)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1)
+    scale = 1e4 / float(clean.mean())
+    I = (torch.poisson(clean.clamp(min=0) * scale, generator=gen) / scale).contiguous()
+    W = torch.ones_like(I)
+    c = (0.5 * c_true).contiguous()
+    return h, c, I, W
+
+
+def run_ours(args):
+    import torch
+    from paper_2504_16446_gb300 import build, synth, tt
+
+    build.build()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    st = synth.workload(WORKLOAD)
+    h, c, I, W = make_inputs(st, torch, tt, synth)
+    g = torch.empty_like(c)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        h.gradient_residual(c, I, W, out=g)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+
+    h.profile(True)
+    h.profile_reset()
+    launches0 = h.launch_count()
+    times = []
+    losses = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record()
+            loss, _ = h.gradient_residual(c, I, W, out=g)
+            ev1.record()
+            ev1.synchronize()
+            times.append(ev0.elapsed_time(ev1))
+            losses.append(loss)
+        torch.cuda.synchronize()
+    launches = h.launch_count() - launches0
+    prof = h.profile_read()
+    h.profile(False)
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+
+    # e2e through the host-buffer entry point: H2D of c, I, W and D2H of g inside the timed region
+    c_h = torch.empty(c.shape, dtype=torch.float32, pin_memory=True)
+    I_h = torch.empty(I.shape, dtype=torch.float32, pin_memory=True)
+    W_h = torch.empty(W.shape, dtype=torch.float32, pin_memory=True)
+    g_h = torch.empty(c.shape, dtype=torch.float32, pin_memory=True)
+    c_h.copy_(c); I_h.copy_(I); W_h.copy_(W)
+    cn, In, Wn, gn = c_h.numpy(), I_h.numpy(), W_h.numpy(), g_h.numpy()
+    for _ in range(2):
+        h.gradient_residual_host(cn, In, Wn, gn)
+    e2e_t = []
+    for _ in range(args.e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.gradient_residual_host(cn, In, Wn, gn)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_t)
+    if dist:
+        t = torch.tensor([e2e_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * args.e2e_steps / e2e_total
+    h2d = (c.numel() + I.numel() + W.numel()) * 4
+    d2h = g.numel() * 4 + 8
+
+    # roofline of the dominant kernel (forward march or adjoint gather)
+    N3 = st.shape[0] * st.shape[1] * st.shape[2]
+    sweep_bytes = st.S * N3 * st.K * 4          # per-projection volume sweep x projections, one direction
+    flops = st.S * st.nj * st.nk * st.shape[0] * st.K * 8   # 4 taps x FMA per channel per plane
+    dom = max(("forward", "adjoint"), key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / max(1, prof[dom][1])
+    peak, peak_kind = peaks()
+    achieved = sweep_bytes / (dom_ms * 1e-3) / 1e9
+    clocks = clk.summary()
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / max(1e-12, sum(x[0] for x in prof.values()))}
+               for k, v in prof.items() if v[1]}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"{world} independent replica(s)", "global_batch": world, "seq_len": None},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": sweep_bytes,
+                     "traffic": ncu_traffic(dom)},
+        "fp32_alu": {"kernel": dom, "achieved_tflops": flops / (dom_ms * 1e-3) / 1e12,
+                     "peak_tflops": fp32_peak, "frac": flops / (dom_ms * 1e-3) / 1e12 / fp32_peak},
+        "kernels": kernels,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "loss": losses[-1],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt, sample = cpu_oracle_rate(st, c.cpu().numpy(), I.cpu().numpy(), W.cpu().numpy(),
+                                           args.cpu_sample_evals)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as it stands, on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2504_16446_gb300 import synth
+
+    st = synth.workload(WORKLOAD)
+    ph = synth.phantom(WORKLOAD)
+    c_true = oracle.zonal_to_sh(st.ell_max, ph.dirs.reshape(-1, 3),
+                                ph.amps.reshape(-1, st.ell_max // 2 + 1)).reshape(st.volume_shape)
+    # data: the oracle's own projection of the phantom with Poisson noise
+    sub_fraction = 0.25     # each step: a quarter of the projections, scaled to the full workload
+    rates = []
+    step_times = []
+    I_full = None
+    for it in range(args.warmup + args.steps):
+        if I_full is None:
+            g_all = oracle.Geometry(st.shape, st.nj, st.nk, st.ell_max, st.inner_angle, st.outer_angle,
+                                    st.seg_start, st.seg_end)
+            I_full = synth.poisson_counts(oracle.forward(g_all, c_true), 1e4, seed=1)
+        rate, dt, sample = cpu_oracle_rate(st, 0.5 * c_true, I_full, np.ones_like(I_full), sub_fraction)
+        if it >= args.warmup:
+            rates.append(rate)
+            step_times.append(dt)
+    total = sum(step_times)
+    evals = len(step_times) * sub_fraction
+    value = evals / total
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD_DESC, "parallelism": "host CPU, 1 thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"per step: {sample}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

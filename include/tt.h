@@ -1,0 +1,190 @@
+/*
+ * tt.h -- C ABI of libtt, the GB300 (sm_103a) gradient-residual engine for
+ * SAXS/WAXS tensor tomography with a real even-order spherical-harmonic basis
+ * (Mumott, arXiv 2504.16446).
+ *
+ * Model (Section "Methodology"):
+ *   I_sjkc = sum_xyz P_sjk,xyz sum_i B_sci c_xyzi           Eq. (forward_model)
+ *   B_sci  = segment mean of Y_i(R_s^T q(phi))               Eq. (projection_matrix)
+ *   r      = A c - I                                         Eq. (residual)
+ *   L      = sum W r^2,  grad L = 2 A^T (W r)                Eq. (opt_prob_general_form), a = 2
+ * P is Joseph's method (Section "Projectors and basis sets"): rays march the
+ * planes of the main axis of their direction, bilinear interpolation of the
+ * four voxel centres around the ray on each plane, zero outside the volume,
+ * step length a/|p_s,m| per plane.  The adjoint is the exact transpose of that
+ * discretisation.
+ *
+ * Conventions shared by every entry point
+ *   - Geometry follows Eq. (real_space_geom) with centred indices: voxel
+ *     (x,y,z) sits at a*(x-(nx-1)/2, y-(ny-1)/2, z-(nz-1)/2) in the sample
+ *     frame; ray (j,k) passes through b*(j-(nj-1)/2-dj) j_s + b*(k-(nk-1)/2-dk) k_s
+ *     with direction p_s, where v_s = R_s^T v and R_s = R_beta(beta_s) R_alpha(alpha_s)
+ *     (right-handed rotations about the outer and inner axes).
+ *   - Real SH: orthonormal, even l only, no Condon-Shortley phase, polar axis +z,
+ *     azimuth from +x towards +y; index i runs over l = 0,2,..,ell_max and
+ *     m = -l..l.  K = (ell_max+1)(ell_max+2)/2.
+ *   - Layouts (row-major, caller-owned DEVICE memory unless stated):
+ *       volume   c[nx][ny][nz][K]      (channel innermost)
+ *       data     I[n_proj][nj][nk][n_seg], weights W with the same layout
+ *       basis    B[n_proj][n_seg][K]   (FP64)
+ *     Every device pointer must be 16-byte aligned (any cudaMalloc / torch
+ *     allocation is).  Internal padding of K is invisible to the caller.
+ *   - Element type: float for a TT_F32 handle, double for a TT_F64 handle
+ *     (entry points with the _f64 suffix).  Calling the other kind returns
+ *     TT_INVALID_ARG.
+ *   - All work is enqueued on the handle's stream, in stream order.  Only
+ *     entry points that return a host value (loss) synchronise that stream.
+ *   - Inputs are never modified, except arguments named *_inout.
+ *   - Errors are returned as tt_status; nothing aborts or throws across the
+ *     ABI.  tt_last_error() gives a message for the calling thread.
+ *   - Handles are not thread-safe; use one handle per host thread.
+ */
+#ifndef TT_H
+#define TT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TT_OK = 0,
+    TT_INVALID_ARG = 1,       /* bad size, pointer, alignment, geometry or precision */
+    TT_UNSUPPORTED = 2,       /* e.g. ell_max outside the compiled set */
+    TT_OUT_OF_MEMORY = 3,     /* device or pinned-host allocation failed */
+    TT_NONFINITE = 4,         /* the loss (hence some input) is NaN or infinite */
+    TT_LINESEARCH_FAILED = 5, /* no Armijo point within the evaluation limit */
+    TT_CUDA_ERROR = 6         /* a CUDA runtime call or kernel launch failed */
+} tt_status;
+
+typedef enum { TT_F32 = 0, TT_F64 = 1 } tt_precision;
+
+/* Unit vectors of the instrument in laboratory coordinates, Table
+ * "geometry_vectors": beam p, raster directions j and k, detector azimuth
+ * origin q0 and +90 deg direction q90, inner (rotation) axis alpha and outer
+ * (tilt) axis beta.  p, j, k must be orthonormal, and so must q0, q90 (both
+ * orthogonal to p); the axes must be non-zero (they are normalised). */
+typedef struct {
+    double p[3], j[3], k[3], q0[3], q90[3], inner_axis[3], outer_axis[3];
+} tt_frame;
+
+/* Problem description, after the paper's data format (Table "h5_format").
+ * All pointers are HOST arrays, copied by tt_create. */
+typedef struct {
+    int nx, ny, nz;              /* volume shape (voxels), each >= 1            */
+    int nj, nk;                  /* raster pixels per projection, each >= 1    */
+    int n_proj;                  /* projections s, >= 1                         */
+    int ell_max;                 /* even band limit, 0..12                      */
+    int n_seg;                   /* detector segments c, 1..64                  */
+    const double *inner_angle;   /* alpha_s [n_proj], radians                   */
+    const double *outer_angle;   /* beta_s  [n_proj], radians                   */
+    const double *j_offset;      /* delta j [n_proj], pixels; NULL = zeros      */
+    const double *k_offset;      /* delta k [n_proj], pixels; NULL = zeros      */
+    const double *seg_start;     /* phi_c,start [n_seg], radians                */
+    const double *seg_end;       /* phi_c,end   [n_seg], radians, > start       */
+    double two_theta;            /* scattering angle 2 theta, radians           */
+    double voxel_size;           /* a > 0                                       */
+    double step_size;            /* b > 0                                       */
+    tt_frame frame;
+} tt_problem;
+
+typedef struct tt_handle tt_handle;
+typedef struct tt_lbfgs tt_lbfgs;
+
+/* Number of even-order real SH coefficients K for a band limit. */
+int tt_num_coeffs(int ell_max);
+const char *tt_status_string(tt_status s);
+/* Message of the last failing call on this host thread ("" if none). */
+const char *tt_last_error(void);
+
+/* Validates the problem, copies it, computes the per-projection ray
+ * constants (host, FP64) and the basis matrix (device, FP64, see
+ * tt_basis_matrix), and allocates the handle's device scratch.  stream is a
+ * cudaStream_t (NULL = legacy default stream); the current CUDA device at
+ * this call is the handle's device.  The handle owns all of its memory. */
+tt_status tt_create(const tt_problem *prob, tt_precision prec, void *stream, tt_handle **out);
+tt_status tt_destroy(tt_handle *h);
+tt_status tt_set_stream(tt_handle *h, void *stream);
+/* Shape query: any out-pointer may be NULL. */
+tt_status tt_get_sizes(const tt_handle *h, int *K, int *K_padded, long long *n_vox, long long *n_data);
+
+/* Eq. (projection_matrix): B[s][c][i] = (1/dphi_c) * integral over segment c
+ * of Y_i(R_s^T q(phi)) dphi, q(phi) = cos(theta)(cos phi q0 + sin phi q90) -
+ * sin(theta) p, theta = two_theta/2, by a 32-node Gauss-Legendre rule per
+ * segment, FP64, on the GPU.  Copies the handle's cached matrix into B_dev
+ * (device, [n_proj][n_seg][K] doubles). */
+tt_status tt_basis_matrix(tt_handle *h, double *B_dev);
+
+/* Forward model, Eq. (forward_model): I = A c.
+ * c_dev [nx][ny][nz][K] -> I_dev [n_proj][nj][nk][n_seg]. */
+tt_status tt_project(tt_handle *h, const float *c_dev, float *I_dev);
+tt_status tt_project_f64(tt_handle *h, const double *c_dev, double *I_dev);
+
+/* Adjoint of the forward model: g = A^T R (SH back-contraction with B_s,
+ * then the exact transpose of the Joseph projection, a gather per voxel with
+ * no atomics).  R_dev [n_proj][nj][nk][n_seg] -> g_dev [nx][ny][nz][K]. */
+tt_status tt_adjoint(tt_handle *h, const float *R_dev, float *g_dev);
+tt_status tt_adjoint_f64(tt_handle *h, const double *R_dev, double *g_dev);
+
+/* Gradient-residual evaluation (Eq. residual with the squared loss):
+ *   r = A c - I,  *loss_host = sum W r^2 (FP64 accumulation),
+ *   g_dev = 2 A^T (W r).
+ * W_dev may be NULL (all weights 1).  g_dev may be NULL (loss only).
+ * loss_host is a HOST pointer; this call synchronises the handle's stream.
+ * Returns TT_NONFINITE (with g and loss written) when the loss is not finite. */
+tt_status tt_gradient_residual(tt_handle *h, const float *c_dev, const float *I_dev,
+                               const float *W_dev, float *g_dev, double *loss_host);
+tt_status tt_gradient_residual_f64(tt_handle *h, const double *c_dev, const double *I_dev,
+                                   const double *W_dev, double *g_dev, double *loss_host);
+
+/* The same evaluation on HOST buffers (c_host, I_host, W_host may be pageable
+ * or pinned; W_host may be NULL): copies the inputs to handle-owned device
+ * buffers, evaluates, and copies the gradient back to g_host.  Synchronous. */
+tt_status tt_gradient_residual_host(tt_handle *h, const float *c_host, const float *I_host,
+                                    const float *W_host, float *g_host, double *loss_host);
+
+/* L-BFGS (Section "Optimization"), unbounded two-loop recursion with memory
+ * m and backtracking Armijo line search (c1 = 1e-4, step halving, at most 20
+ * evaluations per iteration; first iteration steps 1/|g| along -g; a pair is
+ * stored only if s.y > 1e-10 |s||y|; a non-descent direction clears the
+ * memory).  Vectors live on the device in the handle's precision; every dot
+ * product is accumulated in FP64.  I_dev / W_dev (W may be NULL) are
+ * referenced, not copied: keep them alive and unchanged while the state
+ * exists.  tt_lbfgs_create evaluates the loss and gradient at c0_dev. */
+tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0_dev, const void *I_dev,
+                          const void *W_dev, tt_lbfgs **out);
+/* One iteration.  c_out_dev (may be NULL) receives the new iterate
+ * [nx][ny][nz][K]; *loss_host the new loss; *n_evals_host the number of
+ * gradient evaluations used.  On TT_LINESEARCH_FAILED the iterate is
+ * unchanged. */
+tt_status tt_lbfgs_step(tt_handle *h, tt_lbfgs *st, void *c_out_dev, double *loss_host,
+                        int *n_evals_host);
+/* Current iterate / gradient / loss of the state. */
+tt_status tt_lbfgs_get(tt_handle *h, tt_lbfgs *st, void *c_dev, void *g_dev, double *loss_host);
+tt_status tt_lbfgs_destroy(tt_lbfgs *st);
+
+/* Phantom helper: SH coefficients of zonal functions rotated to unit axes n,
+ * c_lm = a_l sqrt(4 pi/(2l+1)) Y_lm(n) (addition theorem).  dirs_dev [n][3],
+ * amps_dev [n][ell_max/2+1], c_dev [n][K], FP32, device, on stream. */
+tt_status tt_zonal_to_sh(int ell_max, long long n, const float *dirs_dev, const float *amps_dev,
+                         float *c_dev, void *stream);
+
+/* Kernel-time accounting.  When enabled, every kernel libtt launches on the
+ * handle's stream is bracketed by CUDA events; tt_profile_read synchronises
+ * and returns, for kernel class `slot`, the summed device time in ms and the
+ * launch count since the last reset.  tt_launch_count counts all kernel
+ * launches of the handle since creation (always on). */
+enum {
+    TT_KSLOT_PACK = 0, TT_KSLOT_FORWARD = 1, TT_KSLOT_BACKCONTRACT = 2, TT_KSLOT_ADJOINT = 3,
+    TT_KSLOT_UNPACK = 4, TT_KSLOT_REDUCE = 5, TT_KSLOT_BASIS = 6, TT_KSLOT_VECTOR = 7,
+    TT_KSLOT_COUNT = 8
+};
+tt_status tt_profile_enable(tt_handle *h, int enable);
+tt_status tt_profile_read(tt_handle *h, int slot, double *total_ms, long long *launches);
+tt_status tt_profile_reset(tt_handle *h);
+const char *tt_kernel_slot_name(int slot);
+long long tt_launch_count(const tt_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TT_H */

@@ -1,0 +1,563 @@
+// tt_api.cu -- C ABI of libtt: validation, geometry set-up (host, FP64),
+// buffer ownership and the orchestration of the kernels on the handle's stream.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "tt_internal.cuh"
+
+namespace tt {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+tt_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? TT_OUT_OF_MEMORY : TT_CUDA_ERROR;
+}
+
+#define TT_CUDA(call, what)                                  \
+    do {                                                     \
+        cudaError_t _e = (call);                             \
+        if (_e != cudaSuccess) return ::tt::cuda_fail(_e, what); \
+    } while (0)
+
+static tt_status invalid(const std::string &msg)
+{
+    set_error(msg);
+    return TT_INVALID_ARG;
+}
+
+void prof_begin(tt_handle *h, int slot, cudaEvent_t *ev)
+{
+    (void)slot;
+    ++h->launch_count;
+    *ev = nullptr;
+    if (!h->prof.enabled) return;
+    cudaEvent_t e;
+    if (!h->prof.free_events.empty()) {
+        e = h->prof.free_events.back();
+        h->prof.free_events.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        return;
+    }
+    cudaEventRecord(e, h->stream);
+    *ev = e;
+}
+
+void prof_end(tt_handle *h, int slot, cudaEvent_t ev)
+{
+    if (!h->prof.enabled || ev == nullptr) return;
+    cudaEvent_t e;
+    if (!h->prof.free_events.empty()) {
+        e = h->prof.free_events.back();
+        h->prof.free_events.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        h->prof.free_events.push_back(ev);
+        return;
+    }
+    cudaEventRecord(e, h->stream);
+    h->prof.pool.push_back(ev);
+    h->prof.pool.push_back(e);
+    h->prof.pool_slot.push_back(slot);
+}
+
+// ---------------------------------------------------------------- geometry
+
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static double norm3(const double *a) { return std::sqrt(dot3(a, a)); }
+
+// Right-handed rotation by angle t about the unit axis n (Rodrigues).
+static void axis_angle(const double *n, double t, double R[9])
+{
+    const double c = std::cos(t), s = std::sin(t), C1 = 1.0 - c;
+    const double x = n[0], y = n[1], z = n[2];
+    R[0] = c + x * x * C1;     R[1] = x * y * C1 - z * s; R[2] = x * z * C1 + y * s;
+    R[3] = y * x * C1 + z * s; R[4] = c + y * y * C1;     R[5] = y * z * C1 - x * s;
+    R[6] = z * x * C1 - y * s; R[7] = z * y * C1 + x * s; R[8] = c + z * z * C1;
+}
+
+static void matmul3(const double A[9], const double B[9], double out[9])
+{
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) out[3 * r + c] = A[3 * r] * B[c] + A[3 * r + 1] * B[3 + c] + A[3 * r + 2] * B[6 + c];
+}
+
+// out = R^T v
+static void apply_transpose(const double R[9], const double *v, double *out)
+{
+    for (int c = 0; c < 3; ++c) out[c] = R[c] * v[0] + R[3 + c] * v[1] + R[6 + c] * v[2];
+}
+
+struct Frames { double p[3], j[3], k[3], q0[3], q90[3]; };
+
+static Frames projection_frames(const tt_handle *h, int s)
+{
+    double ax[3], bx[3];
+    const double na = norm3(h->frame.inner_axis), nb = norm3(h->frame.outer_axis);
+    for (int t = 0; t < 3; ++t) { ax[t] = h->frame.inner_axis[t] / na; bx[t] = h->frame.outer_axis[t] / nb; }
+    double Ra[9], Rb[9], R[9];
+    axis_angle(ax, h->inner[s], Ra);
+    axis_angle(bx, h->outer[s], Rb);
+    matmul3(Rb, Ra, R);                      // R_s = R_beta(beta) R_alpha(alpha)
+    Frames f;
+    apply_transpose(R, h->frame.p, f.p);
+    apply_transpose(R, h->frame.j, f.j);
+    apply_transpose(R, h->frame.k, f.k);
+    apply_transpose(R, h->frame.q0, f.q0);
+    apply_transpose(R, h->frame.q90, f.q90);
+    return f;
+}
+
+static ProjGeom make_geom(const tt_handle *h, int s)
+{
+    const Frames f = projection_frames(h, s);
+    const double *d = f.p;
+    const double mx = std::fmax(std::fabs(d[0]), std::fmax(std::fabs(d[1]), std::fabs(d[2])));
+    int m = 0;
+    while (std::fabs(d[m]) < (1.0 - 1e-12) * mx) ++m;   // ties -> smallest axis
+    const int u = (m == 0) ? 1 : 0;
+    const int v = (m == 2) ? 1 : 2;
+    const int stride[3] = {h->N[1] * h->N[2], h->N[2], 1};
+    const double ba = h->b / h->a;
+    const double cj = 0.5 * (h->nj - 1) + h->joff[s], ck = 0.5 * (h->nk - 1) + h->koff[s];
+    const double hm = 0.5 * (h->N[m] - 1), hu = 0.5 * (h->N[u] - 1), hv = 0.5 * (h->N[v] - 1);
+    ProjGeom g;
+    g.m = m; g.u = u; g.v = v;
+    g.Nm = h->N[m]; g.Nu = h->N[u]; g.Nv = h->N[v];
+    g.sm = stride[m]; g.su = stride[u]; g.sv = stride[v];
+    g.up = d[u] / d[m];
+    g.vp = d[v] / d[m];
+    g.uj = ba * (f.j[u] - f.j[m] * g.up);
+    g.uk = ba * (f.k[u] - f.k[m] * g.up);
+    g.vj = ba * (f.j[v] - f.j[m] * g.vp);
+    g.vk = ba * (f.k[v] - f.k[m] * g.vp);
+    g.u0 = hu - cj * g.uj - ck * g.uk - hm * g.up;
+    g.v0 = hv - cj * g.vj - ck * g.vk - hm * g.vp;
+    g.step = h->a / std::fabs(d[m]);
+    // inverse of the pixel -> plane map [[uj uk],[vj vk]]
+    const double det = g.uj * g.vk - g.uk * g.vj;
+    const double i00 = g.vk / det, i01 = -g.uk / det, i10 = -g.vj / det, i11 = g.uj / det;
+    g.jU = i00; g.jV = i01; g.jP = -(i00 * g.up + i01 * g.vp); g.jc0 = -(i00 * g.u0 + i01 * g.v0);
+    g.kU = i10; g.kV = i11; g.kP = -(i10 * g.up + i11 * g.vp); g.kc0 = -(i10 * g.u0 + i11 * g.v0);
+    const double eps = 1e-3;                 // guards the window against rounding of jc, kc
+    g.hj = std::fabs(i00) + std::fabs(i01) + eps;
+    g.hk = std::fabs(i10) + std::fabs(i11) + eps;
+    g.nwj = (int)std::ceil(2.0 * g.hj);
+    g.nwk = (int)std::ceil(2.0 * g.hk);
+    return g;
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] (Newton on the three-term recurrence).
+static void gauss_legendre(int n, double *x, double *w)
+{
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int l = 2; l <= n; ++l) {
+                const double p2 = ((2 * l - 1) * z * p1 - (l - 1) * p0) / l;
+                p0 = p1; p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-15) {
+                p0 = 1.0; p1 = z;
+                for (int l = 2; l <= n; ++l) {
+                    const double p2 = ((2 * l - 1) * z * p1 - (l - 1) * p0) / l;
+                    p0 = p1; p1 = p2;
+                }
+                dp = n * (z * p1 - p0) / (z * z - 1.0);
+                break;
+            }
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+static bool finite_all(const double *a, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+static tt_status validate(const tt_problem *P)
+{
+    if (!P) return invalid("tt_create: null problem");
+    if (P->nx < 1 || P->ny < 1 || P->nz < 1) return invalid("volume shape must be >= 1 in every axis");
+    if ((long long)P->nx * P->ny * P->nz > (1LL << 31) / 128) return invalid("volume too large");
+    if (P->nj < 1 || P->nk < 1) return invalid("nj, nk must be >= 1");
+    if (P->n_proj < 1) return invalid("n_proj must be >= 1");
+    if (P->ell_max < 0 || (P->ell_max & 1)) return invalid("ell_max must be even and >= 0");
+    if (P->n_seg < 1 || P->n_seg > kMaxSeg) return invalid("n_seg must be in [1, 64]");
+    if (!P->inner_angle || !P->outer_angle || !P->seg_start || !P->seg_end)
+        return invalid("angle and segment arrays must not be NULL");
+    if (!finite_all(P->inner_angle, P->n_proj) || !finite_all(P->outer_angle, P->n_proj))
+        return invalid("rotation/tilt angles must be finite");
+    if ((P->j_offset && !finite_all(P->j_offset, P->n_proj)) || (P->k_offset && !finite_all(P->k_offset, P->n_proj)))
+        return invalid("offsets must be finite");
+    for (int c = 0; c < P->n_seg; ++c)
+        if (!std::isfinite(P->seg_start[c]) || !std::isfinite(P->seg_end[c]) || !(P->seg_end[c] > P->seg_start[c]))
+            return invalid("every segment needs finite seg_end > seg_start");
+    if (!(P->voxel_size > 0) || !(P->step_size > 0) || !std::isfinite(P->voxel_size) || !std::isfinite(P->step_size))
+        return invalid("voxel_size and step_size must be positive and finite");
+    if (!std::isfinite(P->two_theta)) return invalid("two_theta must be finite");
+    const tt_frame &f = P->frame;
+    const double *unit[5] = {f.p, f.j, f.k, f.q0, f.q90};
+    const char *names[5] = {"p", "j", "k", "q0", "q90"};
+    for (int t = 0; t < 5; ++t)
+        if (!(std::fabs(norm3(unit[t]) - 1.0) < 1e-9)) return invalid(std::string("frame vector ") + names[t] + " is not a unit vector");
+    if (!(norm3(f.inner_axis) > 1e-12) || !(norm3(f.outer_axis) > 1e-12) || !std::isfinite(norm3(f.inner_axis)) ||
+        !std::isfinite(norm3(f.outer_axis)))
+        return invalid("rotation axes must be non-zero and finite");
+    if (std::fabs(dot3(f.p, f.j)) > 1e-9 || std::fabs(dot3(f.p, f.k)) > 1e-9 || std::fabs(dot3(f.j, f.k)) > 1e-9)
+        return invalid("p, j, k must be mutually orthogonal");
+    if (std::fabs(dot3(f.p, f.q0)) > 1e-9 || std::fabs(dot3(f.p, f.q90)) > 1e-9 || std::fabs(dot3(f.q0, f.q90)) > 1e-9)
+        return invalid("q0, q90 must be orthogonal to each other and to p");
+    return TT_OK;
+}
+
+static void free_handle(tt_handle *h)
+{
+    if (!h) return;
+    cudaFree(h->geo); cudaFree(h->B64); cudaFree(h->Bp); cudaFree(h->cpad); cudaFree(h->gpad);
+    cudaFree(h->G); cudaFree(h->partials); cudaFree(h->loss_dev);
+    cudaFree(h->hc); cudaFree(h->hI); cudaFree(h->hW); cudaFree(h->hg);
+    if (h->loss_pinned) cudaFreeHost(h->loss_pinned);
+    for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->prof.free_events) cudaEventDestroy(e);
+    delete h;
+}
+
+static long long forward_ctas(const tt_handle *h)
+{
+    const int rays = kThreads / h->LG, TK = 8, TJ = rays / TK;
+    return (long long)((h->nk + TK - 1) / TK) * ((h->nj + TJ - 1) / TJ) * h->S;
+}
+
+// Checks a device pointer argument: non-null, 16-byte aligned.
+static bool bad_ptr(const void *p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
+
+template <typename T>
+static tt_status project_impl(tt_handle *h, const T *c, T *I)
+{
+    if (bad_ptr(c) || bad_ptr(I)) return invalid("tt_project: device pointers must be non-null and 16-byte aligned");
+    TT_CUDA(launch_pack<T>(h, c, (T *)h->cpad), "pack");
+    TT_CUDA(launch_forward<T>(h, (const T *)h->cpad, I, nullptr, nullptr, false), "forward");
+    return TT_OK;
+}
+
+template <typename T>
+static tt_status adjoint_impl(tt_handle *h, const T *R, T *g)
+{
+    if (bad_ptr(R) || bad_ptr(g)) return invalid("tt_adjoint: device pointers must be non-null and 16-byte aligned");
+    TT_CUDA(launch_backcontract<T>(h, R, (T *)h->G), "backcontract");
+    TT_CUDA(launch_adjoint<T>(h, (const T *)h->G, (T *)h->gpad), "adjoint");
+    TT_CUDA(launch_unpack<T>(h, (const T *)h->gpad, g), "unpack");
+    return TT_OK;
+}
+
+}  // namespace tt
+
+using namespace tt;
+
+// Enqueues the gradient-residual evaluation; the loss lands in h->loss_dev.
+template <typename T>
+tt_status tt_grad_enqueue(tt_handle *h, const T *c, const T *I, const T *W, T *g)
+{
+    if (bad_ptr(c) || bad_ptr(I) || (W && bad_ptr(W)) || (g && bad_ptr(g)))
+        return invalid("tt_gradient_residual: device pointers must be non-null (W, g may be NULL) and 16-byte aligned");
+    TT_CUDA(launch_pack<T>(h, c, (T *)h->cpad), "pack");
+    TT_CUDA(launch_forward<T>(h, (const T *)h->cpad, nullptr, I, W, true), "forward");
+    TT_CUDA(launch_reduce(h, h->partials, h->n_partials, h->loss_dev, nullptr, 1.0), "loss reduce");
+    if (g) {
+        TT_CUDA(launch_adjoint<T>(h, (const T *)h->G, (T *)h->gpad), "adjoint");
+        TT_CUDA(launch_unpack<T>(h, (const T *)h->gpad, g), "unpack");
+    }
+    return TT_OK;
+}
+template tt_status tt_grad_enqueue<float>(tt_handle *, const float *, const float *, const float *, float *);
+template tt_status tt_grad_enqueue<double>(tt_handle *, const double *, const double *, const double *, double *);
+
+tt_status tt_read_loss(tt_handle *h, double *loss_host)
+{
+    TT_CUDA(cudaMemcpyAsync(h->loss_pinned, h->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "loss copy");
+    TT_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    const double v = *h->loss_pinned;
+    if (loss_host) *loss_host = v;
+    if (!std::isfinite(v)) {
+        set_error("loss is not finite (NaN/Inf in the inputs)");
+        return TT_NONFINITE;
+    }
+    return TT_OK;
+}
+
+template <typename T>
+static tt_status grad_impl(tt_handle *h, const T *c, const T *I, const T *W, T *g, double *loss_host)
+{
+    if (!loss_host) return invalid("tt_gradient_residual: loss_host must not be NULL");
+    tt_status st = tt_grad_enqueue<T>(h, c, I, W, g);
+    if (st != TT_OK) return st;
+    return tt_read_loss(h, loss_host);
+}
+
+static tt_status check_handle(const tt_handle *h, tt_precision want)
+{
+    if (!h) return invalid("null handle");
+    if (h->prec != want) return invalid("handle precision does not match the entry point (use the _f64 variants with TT_F64)");
+    return TT_OK;
+}
+
+extern "C" {
+
+int tt_num_coeffs(int ell_max) { return ell_max < 0 ? 0 : (ell_max + 1) * (ell_max + 2) / 2; }
+
+const char *tt_status_string(tt_status s)
+{
+    switch (s) {
+    case TT_OK: return "TT_OK";
+    case TT_INVALID_ARG: return "TT_INVALID_ARG";
+    case TT_UNSUPPORTED: return "TT_UNSUPPORTED";
+    case TT_OUT_OF_MEMORY: return "TT_OUT_OF_MEMORY";
+    case TT_NONFINITE: return "TT_NONFINITE";
+    case TT_LINESEARCH_FAILED: return "TT_LINESEARCH_FAILED";
+    case TT_CUDA_ERROR: return "TT_CUDA_ERROR";
+    }
+    return "TT_UNKNOWN";
+}
+
+const char *tt_last_error(void) { return g_last_error.c_str(); }
+
+tt_status tt_create(const tt_problem *P, tt_precision prec, void *stream, tt_handle **out)
+{
+    if (!out) return invalid("tt_create: out must not be NULL");
+    *out = nullptr;
+    tt_status st = validate(P);
+    if (st != TT_OK) return st;
+    if (prec != TT_F32 && prec != TT_F64) return invalid("precision must be TT_F32 or TT_F64");
+    if (P->ell_max > kMaxEll) {
+        set_error("ell_max above 12 has no compiled kernels");
+        return TT_UNSUPPORTED;
+    }
+    tt_handle *h = new (std::nothrow) tt_handle();
+    if (!h) return TT_OUT_OF_MEMORY;
+    h->prec = prec;
+    cudaGetDevice(&h->dev);
+    h->stream = (cudaStream_t)stream;
+    h->N[0] = P->nx; h->N[1] = P->ny; h->N[2] = P->nz;
+    h->nj = P->nj; h->nk = P->nk; h->S = P->n_proj; h->L = P->ell_max; h->C = P->n_seg;
+    h->K = num_coeffs(h->L);
+    h->KP = padded_k(h->K);
+    h->LG = lane_group(h->K);
+    h->CP = (h->C + 3) / 4 * 4;
+    h->a = P->voxel_size; h->b = P->step_size; h->two_theta = P->two_theta;
+    h->frame = P->frame;
+    h->inner.assign(P->inner_angle, P->inner_angle + h->S);
+    h->outer.assign(P->outer_angle, P->outer_angle + h->S);
+    h->joff.assign(h->S, 0.0);
+    h->koff.assign(h->S, 0.0);
+    if (P->j_offset) h->joff.assign(P->j_offset, P->j_offset + h->S);
+    if (P->k_offset) h->koff.assign(P->k_offset, P->k_offset + h->S);
+    h->seg0.assign(P->seg_start, P->seg_start + h->C);
+    h->seg1.assign(P->seg_end, P->seg_end + h->C);
+    h->geo_host.resize(h->S);
+    for (int s = 0; s < h->S; ++s) h->geo_host[s] = make_geom(h, s);
+
+    const size_t es = h->esize();
+#define ALLOC(ptr, bytes)                                                     \
+    do {                                                                      \
+        cudaError_t _e = cudaMalloc((void **)&(ptr), (bytes));                \
+        if (_e != cudaSuccess) { free_handle(h); return cuda_fail(_e, "tt_create: cudaMalloc"); } \
+    } while (0)
+    ALLOC(h->geo, sizeof(ProjGeom) * h->S);
+    ALLOC(h->B64, sizeof(double) * h->S * h->C * h->K);
+    ALLOC(h->Bp, es * h->S * h->CP * h->KP);
+    ALLOC(h->cpad, es * h->nvox() * h->KP);
+    ALLOC(h->gpad, es * h->nvox() * h->KP);
+    ALLOC(h->G, es * h->npix() * h->KP);
+    h->n_partials = forward_ctas(h);
+    if (h->n_partials < kDotBlocks) h->n_partials = kDotBlocks;
+    ALLOC(h->partials, sizeof(double) * h->n_partials);
+    ALLOC(h->loss_dev, sizeof(double) * 4);
+    {
+        cudaError_t e = cudaMallocHost((void **)&h->loss_pinned, sizeof(double) * 4);
+        if (e != cudaSuccess) { free_handle(h); return cuda_fail(e, "tt_create: cudaMallocHost"); }
+    }
+    // basis matrix: stage [nodes][weights][frames 9S][seg0][seg1] and run the quadrature kernel
+    std::vector<double> stage(2 * kQuadNodes + 9 * h->S + 2 * h->C);
+    gauss_legendre(kQuadNodes, stage.data(), stage.data() + kQuadNodes);
+    for (int s = 0; s < h->S; ++s) {
+        const Frames f = projection_frames(h, s);
+        double *F = stage.data() + 2 * kQuadNodes + 9 * s;
+        for (int t = 0; t < 3; ++t) { F[t] = f.p[t]; F[3 + t] = f.q0[t]; F[6 + t] = f.q90[t]; }
+    }
+    std::memcpy(stage.data() + 2 * kQuadNodes + 9 * h->S, h->seg0.data(), sizeof(double) * h->C);
+    std::memcpy(stage.data() + 2 * kQuadNodes + 9 * h->S + h->C, h->seg1.data(), sizeof(double) * h->C);
+    double *dstage = nullptr;
+    ALLOC(dstage, sizeof(double) * stage.size());
+#undef ALLOC
+    cudaError_t e = cudaMemcpyAsync(dstage, stage.data(), sizeof(double) * stage.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->geo, h->geo_host.data(), sizeof(ProjGeom) * h->S, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = launch_basis(h, dstage, dstage + kQuadNodes);
+    if (e == cudaSuccess) e = (prec == TT_F32) ? launch_cast_basis<float>(h) : launch_cast_basis<double>(h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dstage);
+    if (e != cudaSuccess) {
+        free_handle(h);
+        return cuda_fail(e, "tt_create: basis set-up");
+    }
+    *out = h;
+    return TT_OK;
+}
+
+tt_status tt_destroy(tt_handle *h)
+{
+    if (!h) return TT_OK;
+    cudaStreamSynchronize(h->stream);
+    free_handle(h);
+    return TT_OK;
+}
+
+tt_status tt_set_stream(tt_handle *h, void *stream)
+{
+    if (!h) return invalid("null handle");
+    h->stream = (cudaStream_t)stream;
+    return TT_OK;
+}
+
+tt_status tt_get_sizes(const tt_handle *h, int *K, int *KP, long long *n_vox, long long *n_data)
+{
+    if (!h) return invalid("null handle");
+    if (K) *K = h->K;
+    if (KP) *KP = h->KP;
+    if (n_vox) *n_vox = h->nvox() * h->K;
+    if (n_data) *n_data = h->ndata();
+    return TT_OK;
+}
+
+tt_status tt_basis_matrix(tt_handle *h, double *B_dev)
+{
+    if (!h) return invalid("null handle");
+    if (bad_ptr(B_dev)) return invalid("tt_basis_matrix: B_dev must be non-null and 16-byte aligned");
+    TT_CUDA(cudaMemcpyAsync(B_dev, h->B64, sizeof(double) * h->S * h->C * h->K, cudaMemcpyDeviceToDevice, h->stream),
+            "basis copy");
+    return TT_OK;
+}
+
+tt_status tt_project(tt_handle *h, const float *c, float *I)
+{
+    tt_status st = check_handle(h, TT_F32);
+    return st != TT_OK ? st : project_impl<float>(h, c, I);
+}
+
+tt_status tt_project_f64(tt_handle *h, const double *c, double *I)
+{
+    tt_status st = check_handle(h, TT_F64);
+    return st != TT_OK ? st : project_impl<double>(h, c, I);
+}
+
+tt_status tt_adjoint(tt_handle *h, const float *R, float *g)
+{
+    tt_status st = check_handle(h, TT_F32);
+    return st != TT_OK ? st : adjoint_impl<float>(h, R, g);
+}
+
+tt_status tt_adjoint_f64(tt_handle *h, const double *R, double *g)
+{
+    tt_status st = check_handle(h, TT_F64);
+    return st != TT_OK ? st : adjoint_impl<double>(h, R, g);
+}
+
+tt_status tt_gradient_residual(tt_handle *h, const float *c, const float *I, const float *W, float *g,
+                               double *loss_host)
+{
+    tt_status st = check_handle(h, TT_F32);
+    return st != TT_OK ? st : grad_impl<float>(h, c, I, W, g, loss_host);
+}
+
+tt_status tt_gradient_residual_f64(tt_handle *h, const double *c, const double *I, const double *W, double *g,
+                                   double *loss_host)
+{
+    tt_status st = check_handle(h, TT_F64);
+    return st != TT_OK ? st : grad_impl<double>(h, c, I, W, g, loss_host);
+}
+
+tt_status tt_gradient_residual_host(tt_handle *h, const float *c_host, const float *I_host, const float *W_host,
+                                    float *g_host, double *loss_host)
+{
+    tt_status st = check_handle(h, TT_F32);
+    if (st != TT_OK) return st;
+    if (!c_host || !I_host || !g_host || !loss_host)
+        return invalid("tt_gradient_residual_host: c, I, g, loss must not be NULL");
+    const size_t bc = sizeof(float) * h->nvox() * h->K, bd = sizeof(float) * h->ndata();
+    if (!h->hc) TT_CUDA(cudaMalloc(&h->hc, bc), "host-path cudaMalloc");
+    if (!h->hg) TT_CUDA(cudaMalloc(&h->hg, bc), "host-path cudaMalloc");
+    if (!h->hI) TT_CUDA(cudaMalloc(&h->hI, bd), "host-path cudaMalloc");
+    if (W_host && !h->hW) TT_CUDA(cudaMalloc(&h->hW, bd), "host-path cudaMalloc");
+    TT_CUDA(cudaMemcpyAsync(h->hc, c_host, bc, cudaMemcpyHostToDevice, h->stream), "H2D c");
+    TT_CUDA(cudaMemcpyAsync(h->hI, I_host, bd, cudaMemcpyHostToDevice, h->stream), "H2D I");
+    if (W_host) TT_CUDA(cudaMemcpyAsync(h->hW, W_host, bd, cudaMemcpyHostToDevice, h->stream), "H2D W");
+    st = tt_grad_enqueue<float>(h, (const float *)h->hc, (const float *)h->hI, W_host ? (const float *)h->hW : nullptr,
+                                (float *)h->hg);
+    if (st != TT_OK) return st;
+    TT_CUDA(cudaMemcpyAsync(g_host, h->hg, bc, cudaMemcpyDeviceToHost, h->stream), "D2H g");
+    return tt_read_loss(h, loss_host);
+}
+
+tt_status tt_profile_enable(tt_handle *h, int enable)
+{
+    if (!h) return invalid("null handle");
+    h->prof.enabled = enable != 0;
+    return TT_OK;
+}
+
+tt_status tt_profile_reset(tt_handle *h)
+{
+    if (!h) return invalid("null handle");
+    TT_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    for (cudaEvent_t e : h->prof.pool) h->prof.free_events.push_back(e);
+    h->prof.pool.clear();
+    h->prof.pool_slot.clear();
+    for (int i = 0; i < TT_KSLOT_COUNT; ++i) { h->prof.total_ms[i] = 0.0; h->prof.launches[i] = 0; }
+    return TT_OK;
+}
+
+tt_status tt_profile_read(tt_handle *h, int slot, double *total_ms, long long *launches)
+{
+    if (!h) return invalid("null handle");
+    if (slot < 0 || slot >= TT_KSLOT_COUNT) return invalid("bad kernel slot");
+    if (!h->prof.pool.empty()) {
+        TT_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+        for (size_t i = 0; i < h->prof.pool_slot.size(); ++i) {
+            float ms = 0.f;
+            TT_CUDA(cudaEventElapsedTime(&ms, h->prof.pool[2 * i], h->prof.pool[2 * i + 1]), "event elapsed");
+            h->prof.total_ms[h->prof.pool_slot[i]] += ms;
+            h->prof.launches[h->prof.pool_slot[i]] += 1;
+        }
+        for (cudaEvent_t e : h->prof.pool) h->prof.free_events.push_back(e);
+        h->prof.pool.clear();
+        h->prof.pool_slot.clear();
+    }
+    if (total_ms) *total_ms = h->prof.total_ms[slot];
+    if (launches) *launches = h->prof.launches[slot];
+    return TT_OK;
+}
+
+const char *tt_kernel_slot_name(int slot)
+{
+    static const char *names[TT_KSLOT_COUNT] = {"pack", "forward", "backcontract", "adjoint",
+                                                "unpack", "reduce", "basis", "vector"};
+    return (slot >= 0 && slot < TT_KSLOT_COUNT) ? names[slot] : "";
+}
+
+long long tt_launch_count(const tt_handle *h) { return h ? h->launch_count : 0; }
+
+}  // extern "C"

@@ -1,0 +1,130 @@
+// tt_internal.cuh -- shared declarations of libtt (handle, per-projection
+// ray constants, kernel launchers).  Host code is C++17, device code sm_103a.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tt.h"
+
+namespace tt {
+
+// Largest band limit with compiled kernels and its coefficient count.
+constexpr int kMaxEll = 12;
+constexpr int kMaxSeg = 64;
+constexpr int kQuadNodes = 32;      // Gauss-Legendre nodes per detector segment
+constexpr int kThreads = 256;       // threads per CTA of the projector kernels
+
+// Lane-group width (lanes that share one ray or one voxel, each holding
+// KP/LG channels) and padded channel count for a band limit.
+__host__ __device__ constexpr int lane_group(int K) { return K <= 4 ? 1 : (K <= 8 ? 2 : 4); }
+__host__ __device__ constexpr int padded_k(int K) {
+    return ((K + 4 * lane_group(K) - 1) / (4 * lane_group(K))) * (4 * lane_group(K));
+}
+__host__ __device__ constexpr int num_coeffs(int L) { return (L + 1) * (L + 2) / 2; }
+
+// Per-projection constants of the Joseph discretisation, in voxel-index
+// units (computed on the host in FP64 from Eq. real_space_geom).
+//   plane p (index along the main axis m), ray (j,k):
+//     u(j,k,p) = u0 + j*uj + k*uk + p*up   (continuous index along axis u)
+//     v(j,k,p) = v0 + j*vj + k*vk + p*vp   (continuous index along axis v)
+//   adjoint: the ray lattice point nearest to voxel (U,V) on plane p is
+//     jc = jc0 + jU*U + jV*V + jP*p,  kc = kc0 + kU*U + kV*V + kP*p,
+//   and every ray that has (U,V) as a bilinear tap lies in
+//     |j - jc| < hj, |k - kc| < hk   (at most nwj x nwk candidates).
+struct ProjGeom {
+    double u0, uj, uk, up;
+    double v0, vj, vk, vp;
+    double step;              // a / |p_s,m|
+    double jc0, jU, jV, jP;
+    double kc0, kU, kV, kP;
+    double hj, hk;
+    int m, u, v;              // main and transverse axes (0=x, 1=y, 2=z)
+    int Nm, Nu, Nv;
+    int sm, su, sv;           // voxel strides of the axes
+    int nwj, nwk;
+};
+
+struct Profile {
+    bool enabled = false;
+    std::vector<cudaEvent_t> pool;     // recorded pairs awaiting read
+    std::vector<int> pool_slot;
+    std::vector<cudaEvent_t> free_events;
+    double total_ms[TT_KSLOT_COUNT] = {};
+    long long launches[TT_KSLOT_COUNT] = {};
+};
+
+}  // namespace tt
+
+struct tt_handle {
+    tt_precision prec;
+    int dev;
+    cudaStream_t stream;
+    int N[3];
+    int nj, nk, S, L, K, KP, LG, C, CP;
+    double a, b, two_theta;
+    std::vector<double> inner, outer, joff, koff, seg0, seg1;
+    tt_frame frame;
+    std::vector<tt::ProjGeom> geo_host;
+    tt::ProjGeom *geo = nullptr;        // device [S]
+    double *B64 = nullptr;               // device [S][C][K] FP64
+    void *Bp = nullptr;                  // device [S][CP][KP], element type, zero padded
+    void *cpad = nullptr;                // device [nvox][KP]
+    void *gpad = nullptr;                // device [nvox][KP]
+    void *G = nullptr;                   // device [S][nj][nk][KP]
+    double *partials = nullptr;          // device, per-CTA loss partials
+    long long n_partials = 0;
+    double *loss_dev = nullptr;          // device scalar
+    double *loss_pinned = nullptr;       // pinned host scalar
+    // host-buffer entry point staging (allocated on first use)
+    void *hc = nullptr, *hI = nullptr, *hW = nullptr, *hg = nullptr;
+    long long launch_count = 0;
+    tt::Profile prof;
+
+    long long nvox() const { return (long long)N[0] * N[1] * N[2]; }
+    long long npix() const { return (long long)S * nj * nk; }
+    long long ndata() const { return npix() * C; }
+    size_t esize() const { return prec == TT_F64 ? 8 : 4; }
+};
+
+namespace tt {
+
+void set_error(const std::string &msg);
+tt_status cuda_fail(cudaError_t e, const char *what);
+
+// Bracket a kernel launch with the handle's profiling events.
+void prof_begin(tt_handle *h, int slot, cudaEvent_t *ev);
+void prof_end(tt_handle *h, int slot, cudaEvent_t ev);
+
+// Kernel launchers (return the launch error, if any).
+template <typename T>
+cudaError_t launch_pack(tt_handle *h, const T *c, T *cpad);
+template <typename T>
+cudaError_t launch_unpack(tt_handle *h, const T *gpad, T *g);
+template <typename T>
+cudaError_t launch_forward(tt_handle *h, const T *cpad, T *Iout, const T *I, const T *W, bool grad);
+template <typename T>
+cudaError_t launch_backcontract(tt_handle *h, const T *R, T *G);
+template <typename T>
+cudaError_t launch_adjoint(tt_handle *h, const T *G, T *gpad);
+cudaError_t launch_reduce(tt_handle *h, const double *partials, long long n, double *out,
+                          const double *add, double mul);
+cudaError_t launch_basis(tt_handle *h, const double *nodes, const double *weights);
+template <typename T>
+cudaError_t launch_cast_basis(tt_handle *h);
+
+// FP64-accumulated vector kernels for the optimizer.
+template <typename T>
+cudaError_t vec_dot(tt_handle *h, const T *x, const T *y, long long n, double *partials,
+                    double *out, const double *add, double mul);
+// y = a*x + b*y with a = ha * (da ? *da : 1), b = hb
+template <typename T>
+cudaError_t vec_axpby(tt_handle *h, T *y, const T *x, long long n, double ha, const double *da, double hb);
+template <typename T>
+cudaError_t vec_sub(tt_handle *h, T *out, const T *x, const T *y, long long n);
+constexpr int kDotBlocks = 608;   // 4 x 152 SMs
+
+}  // namespace tt

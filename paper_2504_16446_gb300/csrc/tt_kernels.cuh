@@ -1,0 +1,433 @@
+// tt_kernels.cuh -- projector kernels of libtt (templates; instantiated per
+// element type in tt_proj_f32.cu / tt_proj_f64.cu).
+//
+// Data layout in HBM (all row-major):
+//   cpad [nx][ny][nz][KP]          coefficient volume, channel innermost, zero padded
+//   Bp   [S][CP][KP]               basis matrix in the element type, zero padded
+//   G    [S][nj][nk][KP]           back-contracted weighted residual, 2 B_s^T (W r)
+//   gpad [nx][ny][nz][KP]          gradient / adjoint volume
+// A lane group of LG consecutive lanes owns one ray (forward) or one voxel
+// (adjoint); lane q of the group holds channels [q*CPL, (q+1)*CPL), so that a
+// bilinear tap is one contiguous KP-element row read by LG lanes with 16-byte
+// vector loads.
+#pragma once
+
+#include "tt_internal.cuh"
+
+namespace tt {
+
+// ----------------------------------------------------------- vector helpers
+
+template <typename T, int CPL>
+__device__ __forceinline__ void fma_row(T (&acc)[CPL], T w, const T *__restrict__ p)
+{
+    if constexpr (sizeof(T) == 4) {
+        static_assert(CPL % 4 == 0, "float rows are read as float4");
+#pragma unroll
+        for (int t = 0; t < CPL / 4; ++t) {
+            float4 x = __ldg(reinterpret_cast<const float4 *>(p) + t);
+            acc[4 * t + 0] = fmaf(w, x.x, acc[4 * t + 0]);
+            acc[4 * t + 1] = fmaf(w, x.y, acc[4 * t + 1]);
+            acc[4 * t + 2] = fmaf(w, x.z, acc[4 * t + 2]);
+            acc[4 * t + 3] = fmaf(w, x.w, acc[4 * t + 3]);
+        }
+    } else {
+        static_assert(CPL % 2 == 0, "double rows are read as double2");
+#pragma unroll
+        for (int t = 0; t < CPL / 2; ++t) {
+            double2 x = __ldg(reinterpret_cast<const double2 *>(p) + t);
+            acc[2 * t + 0] = fma(w, x.x, acc[2 * t + 0]);
+            acc[2 * t + 1] = fma(w, x.y, acc[2 * t + 1]);
+        }
+    }
+}
+
+template <typename T, int CPL>
+__device__ __forceinline__ void store_row(T *__restrict__ p, const T (&v)[CPL], T scale)
+{
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int t = 0; t < CPL / 4; ++t)
+            reinterpret_cast<float4 *>(p)[t] =
+                make_float4(scale * v[4 * t], scale * v[4 * t + 1], scale * v[4 * t + 2], scale * v[4 * t + 3]);
+    } else {
+#pragma unroll
+        for (int t = 0; t < CPL / 2; ++t)
+            reinterpret_cast<double2 *>(p)[t] = make_double2(scale * v[2 * t], scale * v[2 * t + 1]);
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Deterministic block sum (fixed order) of one double per thread; result in
+// thread 0.
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
+        t = warp_sum(t);
+    }
+    return t;
+}
+
+// Range of planes p in [0, Nm-1] on which coordinate w(p) = w0 + p*dw can
+// give a tap inside [0, N-1] (i.e. -1 < w < N), widened by one plane on each
+// side; per-tap bounds checks make the widening harmless.
+template <typename T>
+__device__ __forceinline__ void clip_planes(T w0, T dw, int N, T &lo, T &hi)
+{
+    if (fabs(dw) < T(1e-12)) {
+        if (!(w0 > T(-1) && w0 < T(N))) { lo = T(1); hi = T(0); }
+        return;
+    }
+    T inv = T(1) / dw;
+    T p1 = (T(-1) - w0) * inv, p2 = (T(N) - w0) * inv;
+    lo = fmax(lo, fmin(p1, p2) - T(1));
+    hi = fmin(hi, fmax(p1, p2) + T(1));
+}
+
+// ------------------------------------------------------------ forward kernel
+//
+// One CTA = one projection s x one 8-wide tile of rays.  Each lane group
+// marches its ray along the main axis (Joseph's method, bilinear taps read
+// straight from the L1/L2-resident volume), scales by the step length, then
+//   PROJECT: writes I_hat = B_s Y                           (Eq. forward_model)
+//   GRAD:    r = I_hat - I, loss += W r^2, G = 2 B_s^T (W r) (Eq. residual)
+// The SH contraction runs four segments at a time: partial dot products over
+// the lane's channels, a butterfly across the lane group, then each lane
+// back-contracts into its own channels.
+template <typename T, int KP, int LG, bool GRAD>
+__global__ void __launch_bounds__(kThreads)
+k_forward(const ProjGeom *__restrict__ geo, const T *__restrict__ cpad, const T *__restrict__ Bp,
+          int nj, int nk, int C, int CP, int tiles_k,
+          T *__restrict__ Iout, const T *__restrict__ Id, const T *__restrict__ Wd,
+          T *__restrict__ G, double *__restrict__ partials)
+{
+    constexpr int CPL = KP / LG;
+    constexpr int RAYS = kThreads / LG;
+    constexpr int TK = 8;
+    constexpr int TJ = RAYS / TK;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Bs = reinterpret_cast<T *>(smem_raw);   // [CP][KP]
+    __shared__ double red[kThreads / 32];
+
+    const int s = blockIdx.y;
+    const int tj = blockIdx.x / tiles_k, tk = blockIdx.x % tiles_k;
+    const int r = threadIdx.x / LG, q = threadIdx.x % LG;
+    const int j = tj * TJ + r / TK, k = tk * TK + r % TK;
+    const bool valid = (j < nj) && (k < nk);
+
+    const T *Bsrc = Bp + (size_t)s * CP * KP;
+    for (int t = threadIdx.x; t < CP * KP; t += kThreads) Bs[t] = Bsrc[t];
+
+    const ProjGeom &P = geo[s];
+    // Ray base in FP64 (one rounding to T), per-plane stepping in T.
+    const double urd = P.u0 + (double)j * P.uj + (double)k * P.uk;
+    const double vrd = P.v0 + (double)j * P.vj + (double)k * P.vk;
+    const T ur = (T)urd, vr = (T)vrd, up = (T)P.up, vp = (T)P.vp;
+    const int Nu = P.Nu, Nv = P.Nv, sm = P.sm, su = P.su, sv = P.sv;
+    T lo = T(0), hi = T(P.Nm - 1);
+    clip_planes<T>(ur, up, Nu, lo, hi);
+    clip_planes<T>(vr, vp, Nv, lo, hi);
+    int plo = valid ? max(0, (int)floor(lo)) : 1;
+    int phi = valid ? min(P.Nm - 1, (int)ceil(hi)) : 0;
+
+    T acc[CPL];
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) acc[i] = T(0);
+    const T *cq = cpad + q * CPL;
+    for (int p = plo; p <= phi; ++p) {
+        const T u = fma((T)p, up, ur), v = fma((T)p, vp, vr);
+        const T fu = floor(u), fv = floor(v);
+        const int iu = (int)fu, iv = (int)fv;
+        const T wu = u - fu, wv = v - fv;
+        const bool u0 = (unsigned)iu < (unsigned)Nu, u1 = (unsigned)(iu + 1) < (unsigned)Nu;
+        const bool v0 = (unsigned)iv < (unsigned)Nv, v1 = (unsigned)(iv + 1) < (unsigned)Nv;
+        const long long vox = (long long)p * sm + (long long)iu * su + (long long)iv * sv;
+        if (u0 && v0) fma_row<T, CPL>(acc, (T(1) - wu) * (T(1) - wv), cq + vox * KP);
+        if (u1 && v0) fma_row<T, CPL>(acc, wu * (T(1) - wv), cq + (vox + su) * KP);
+        if (u0 && v1) fma_row<T, CPL>(acc, (T(1) - wu) * wv, cq + (vox + sv) * KP);
+        if (u1 && v1) fma_row<T, CPL>(acc, wu * wv, cq + (vox + su + sv) * KP);
+    }
+    const T step = (T)P.step;
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) acc[i] *= step;
+
+    __syncthreads();   // Bs staged
+
+    const long long pix = ((long long)s * nj + j) * nk + k;
+    T gacc[CPL];
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) gacc[i] = T(0);
+    T lossr = T(0);
+    const bool vec4 = (C % 4) == 0;
+    for (int c0 = 0; c0 < CP; c0 += 4) {
+        T ih[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const T *brow = Bs + (c0 + t) * KP + q * CPL;
+            T sacc = T(0);
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) sacc = fma(brow[i], acc[i], sacc);
+            ih[t] = sacc;
+        }
+#pragma unroll
+        for (int off = LG / 2; off > 0; off >>= 1)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) ih[t] += __shfl_xor_sync(0xffffffffu, ih[t], off);
+        if constexpr (!GRAD) {
+            if (valid) {
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if ((t % LG) == q && c0 + t < C) Iout[pix * C + c0 + t] = ih[t];
+            }
+        } else {
+            T dI[4] = {T(0), T(0), T(0), T(0)}, dW[4] = {T(1), T(1), T(1), T(1)};
+            if (valid) {
+                const long long o = pix * C + c0;
+                if (vec4) {
+                    if constexpr (sizeof(T) == 4) {
+                        float4 a = __ldg(reinterpret_cast<const float4 *>(Id + o));
+                        dI[0] = a.x; dI[1] = a.y; dI[2] = a.z; dI[3] = a.w;
+                        if (Wd) {
+                            float4 b = __ldg(reinterpret_cast<const float4 *>(Wd + o));
+                            dW[0] = b.x; dW[1] = b.y; dW[2] = b.z; dW[3] = b.w;
+                        }
+                    } else {
+                        double2 a0 = __ldg(reinterpret_cast<const double2 *>(Id + o));
+                        double2 a1 = __ldg(reinterpret_cast<const double2 *>(Id + o) + 1);
+                        dI[0] = a0.x; dI[1] = a0.y; dI[2] = a1.x; dI[3] = a1.y;
+                        if (Wd) {
+                            double2 b0 = __ldg(reinterpret_cast<const double2 *>(Wd + o));
+                            double2 b1 = __ldg(reinterpret_cast<const double2 *>(Wd + o) + 1);
+                            dW[0] = b0.x; dW[1] = b0.y; dW[2] = b1.x; dW[3] = b1.y;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (c0 + t < C) {
+                            dI[t] = __ldg(Id + o + t);
+                            if (Wd) dW[t] = __ldg(Wd + o + t);
+                        }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const bool live = valid && (c0 + t < C);
+                const T rr = live ? ih[t] - dI[t] : T(0);
+                const T wr = live ? dW[t] * rr : T(0);
+                lossr = fma(wr, rr, lossr);
+                const T *brow = Bs + (c0 + t) * KP + q * CPL;
+#pragma unroll
+                for (int i = 0; i < CPL; ++i) gacc[i] = fma(brow[i], wr, gacc[i]);
+            }
+        }
+    }
+    if constexpr (GRAD) {
+        if (valid) store_row<T, CPL>(G + pix * KP + q * CPL, gacc, T(2));
+        const double lv = (q == 0 && valid) ? (double)lossr : 0.0;
+        const double tot = block_sum(lv, red);
+        if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
+// ----------------------------------------------------- back-contraction
+// G[pix][i] = sum_c B[s][c][i] R[pix][c]  (the SH part of A^T).
+template <typename T, int KP, int LG>
+__global__ void __launch_bounds__(kThreads)
+k_backcontract(const T *__restrict__ Bp, const T *__restrict__ R, T *__restrict__ G,
+               long long npix, int njk, int C, int CP)
+{
+    constexpr int CPL = KP / LG;
+    constexpr int RAYS = kThreads / LG;
+    const int r = threadIdx.x / LG, q = threadIdx.x % LG;
+    const long long pix = (long long)blockIdx.x * RAYS + r;
+    if (pix >= npix) return;
+    const int s = (int)(pix / njk);
+    const T *B = Bp + (size_t)s * CP * KP + q * CPL;
+    T acc[CPL];
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) acc[i] = T(0);
+    for (int c = 0; c < C; ++c) {
+        const T rc = __ldg(R + pix * C + c);
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) acc[i] = fma(__ldg(B + c * KP + i), rc, acc[i]);
+    }
+    store_row<T, CPL>(G + pix * KP + q * CPL, acc, T(1));
+}
+
+__device__ __forceinline__ int sel3(int x, int y, int z, int axis)
+{
+    return axis == 0 ? x : (axis == 1 ? y : z);
+}
+
+// ---------------------------------------------------------- adjoint kernel
+//
+// Exact transpose of k_forward's Joseph discretisation, as a gather: one lane
+// group per voxel, looping over all projections; on the voxel's plane of
+// projection s it visits the rays whose bilinear footprint contains the voxel
+// (|u - U| < 1 and |v - V| < 1, weight (1-|du|)(1-|dv|) * step, the same
+// weight the forward gave this tap) and accumulates their G rows.  Every
+// voxel is written once; no atomics.
+template <typename T>
+struct AdjConst {
+    T jc0, jU, jV, jP, kc0, kU, kV, kP, hj, hk;
+    T u0, up, uj, uk, v0, vp, vj, vk, step;
+    int m, u, v, nwj, nwk;
+};
+
+constexpr int kAdjChunk = 128;   // projections staged in shared memory at a time
+
+template <typename T, int KP, int LG>
+__global__ void __launch_bounds__(kThreads)
+k_adjoint(const ProjGeom *__restrict__ geo, int S, const T *__restrict__ G, int nj, int nk,
+          int nx, int ny, int nz, int ty, int tz, T *__restrict__ gpad)
+{
+    constexpr int CPL = KP / LG;
+    constexpr int VOX = kThreads / LG;
+    constexpr int BZ = 4, BY = 4, BX = VOX / 16;
+    __shared__ AdjConst<T> cs[kAdjChunk];
+
+    const int b = blockIdx.x;
+    const int bz = b % tz, by = (b / tz) % ty, bx = b / (tz * ty);
+    const int r = threadIdx.x / LG, q = threadIdx.x % LG;
+    const int x = bx * BX + r / (BY * BZ), y = by * BY + (r / BZ) % BY, z = bz * BZ + r % BZ;
+    const bool valid = (x < nx) && (y < ny) && (z < nz);
+
+    T acc[CPL];
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) acc[i] = T(0);
+    const size_t gstride = (size_t)nj * nk * KP;
+
+    for (int s0 = 0; s0 < S; s0 += kAdjChunk) {
+        const int ns = min(kAdjChunk, S - s0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < ns; t += kThreads) {
+            const ProjGeom &P = geo[s0 + t];
+            AdjConst<T> c;
+            c.jc0 = (T)P.jc0; c.jU = (T)P.jU; c.jV = (T)P.jV; c.jP = (T)P.jP;
+            c.kc0 = (T)P.kc0; c.kU = (T)P.kU; c.kV = (T)P.kV; c.kP = (T)P.kP;
+            c.hj = (T)P.hj; c.hk = (T)P.hk;
+            c.u0 = (T)P.u0; c.up = (T)P.up; c.uj = (T)P.uj; c.uk = (T)P.uk;
+            c.v0 = (T)P.v0; c.vp = (T)P.vp; c.vj = (T)P.vj; c.vk = (T)P.vk;
+            c.step = (T)P.step;
+            c.m = P.m; c.u = P.u; c.v = P.v; c.nwj = P.nwj; c.nwk = P.nwk;
+            cs[t] = c;
+        }
+        __syncthreads();
+        for (int si = 0; si < ns; ++si) {
+            const AdjConst<T> &c = cs[si];
+            const T fp = (T)sel3(x, y, z, c.m), fU = (T)sel3(x, y, z, c.u), fV = (T)sel3(x, y, z, c.v);
+            const T jc = c.jc0 + c.jU * fU + c.jV * fV + c.jP * fp;
+            const T kc = c.kc0 + c.kU * fU + c.kV * fV + c.kP * fp;
+            const T bu = (c.u0 - fU) + c.up * fp, bv = (c.v0 - fV) + c.vp * fp;
+            const int j0 = (int)floor(jc - c.hj) + 1, k0 = (int)floor(kc - c.hk) + 1;
+            const T *Gs = G + (size_t)(s0 + si) * gstride + q * CPL;
+            for (int a = 0; a < c.nwj; ++a) {
+                const int jj = j0 + a;
+                T du = bu + (T)jj * c.uj + (T)k0 * c.uk;
+                T dv = bv + (T)jj * c.vj + (T)k0 * c.vk;
+                for (int bb = 0; bb < c.nwk; ++bb) {
+                    const int kk = k0 + bb;
+                    const T adu = fabs(du), adv = fabs(dv);
+                    if (valid && adu < T(1) && adv < T(1) && (unsigned)jj < (unsigned)nj &&
+                        (unsigned)kk < (unsigned)nk) {
+                        const T w = (T(1) - adu) * (T(1) - adv) * c.step;
+                        fma_row<T, CPL>(acc, w, Gs + ((size_t)jj * nk + kk) * KP);
+                    }
+                    du += c.uk;
+                    dv += c.vk;
+                }
+            }
+        }
+    }
+    if (valid) {
+        const long long vox = ((long long)x * ny + y) * nz + z;
+        store_row<T, CPL>(gpad + vox * KP + q * CPL, acc, T(1));
+    }
+}
+
+// ------------------------------------------------------------ launchers
+
+template <typename T, int L>
+cudaError_t launch_forward_L(tt_handle *h, const T *cpad, T *Iout, const T *I, const T *W, bool grad)
+{
+    constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K);
+    constexpr int RAYS = kThreads / LG, TK = 8, TJ = RAYS / TK;
+    const int tiles_k = (h->nk + TK - 1) / TK, tiles_j = (h->nj + TJ - 1) / TJ;
+    dim3 grid(tiles_k * tiles_j, h->S);
+    const size_t smem = (size_t)h->CP * KP * sizeof(T);
+    const T *Bp = (const T *)h->Bp;
+    cudaEvent_t ev;
+    prof_begin(h, TT_KSLOT_FORWARD, &ev);
+    if (grad) {
+        auto kern = k_forward<T, KP, LG, true>;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<grid, kThreads, smem, h->stream>>>(h->geo, cpad, Bp, h->nj, h->nk, h->C, h->CP, tiles_k,
+                                                 nullptr, I, W, (T *)h->G, h->partials);
+    } else {
+        auto kern = k_forward<T, KP, LG, false>;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<grid, kThreads, smem, h->stream>>>(h->geo, cpad, Bp, h->nj, h->nk, h->C, h->CP, tiles_k,
+                                                 Iout, nullptr, nullptr, nullptr, nullptr);
+    }
+    cudaError_t e = cudaGetLastError();
+    prof_end(h, TT_KSLOT_FORWARD, ev);
+    return e;
+}
+
+template <typename T, int L>
+cudaError_t launch_backcontract_L(tt_handle *h, const T *R, T *G)
+{
+    constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K);
+    constexpr int RAYS = kThreads / LG;
+    const long long npix = h->npix();
+    const unsigned blocks = (unsigned)((npix + RAYS - 1) / RAYS);
+    cudaEvent_t ev;
+    prof_begin(h, TT_KSLOT_BACKCONTRACT, &ev);
+    k_backcontract<T, KP, LG><<<blocks, kThreads, 0, h->stream>>>((const T *)h->Bp, R, G, npix,
+                                                                 h->nj * h->nk, h->C, h->CP);
+    cudaError_t e = cudaGetLastError();
+    prof_end(h, TT_KSLOT_BACKCONTRACT, ev);
+    return e;
+}
+
+template <typename T, int L>
+cudaError_t launch_adjoint_L(tt_handle *h, const T *G, T *gpad)
+{
+    constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K);
+    constexpr int VOX = kThreads / LG, BZ = 4, BY = 4, BX = VOX / 16;
+    const int tx = (h->N[0] + BX - 1) / BX, ty = (h->N[1] + BY - 1) / BY, tz = (h->N[2] + BZ - 1) / BZ;
+    cudaEvent_t ev;
+    prof_begin(h, TT_KSLOT_ADJOINT, &ev);
+    k_adjoint<T, KP, LG><<<(unsigned)(tx * ty * tz), kThreads, 0, h->stream>>>(
+        h->geo, h->S, G, h->nj, h->nk, h->N[0], h->N[1], h->N[2], ty, tz, gpad);
+    cudaError_t e = cudaGetLastError();
+    prof_end(h, TT_KSLOT_ADJOINT, ev);
+    return e;
+}
+
+#define TT_DISPATCH_L(L, CALL)                       \
+    switch (L) {                                     \
+    case 0: return CALL(0);                          \
+    case 2: return CALL(2);                          \
+    case 4: return CALL(4);                          \
+    case 6: return CALL(6);                          \
+    case 8: return CALL(8);                          \
+    case 10: return CALL(10);                        \
+    case 12: return CALL(12);                        \
+    default: return cudaErrorInvalidValue;           \
+    }
+
+}  // namespace tt

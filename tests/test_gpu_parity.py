@@ -1,0 +1,215 @@
+"""GPU parity: libtt (through its C ABI) against the FP64 oracle.
+
+Tolerances: relative L2 <= 1e-5 for FP32 results, <= 1e-12 for the FP64
+build (basis matrix 1e-13 absolute), on identical seeded inputs.  Sizes span
+several CTA tiles with ragged tails (non-multiple-of-8 detector sizes,
+non-cubic volumes, segment counts that are not multiples of 4, sub-pixel
+offsets, tilts up to 60 degrees).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2504_16446_gb300 import synth
+from paper_2504_16446_gb300 import tt
+from conftest import oracle_geometry
+
+pytestmark = pytest.mark.gpu
+
+F32_TOL = 1e-5
+F64_TOL = 1e-12
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(x, dtype):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2504_16446_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+SMALL = [
+    dict(n=(6, 5, 7), nj=7, nk=6, ell_max=2, n_proj=5, n_seg=4, seed=0),
+    dict(n=(12, 9, 10), nj=13, nk=11, ell_max=4, n_proj=9, n_seg=5, seed=1),
+    dict(n=(9, 9, 9), nj=17, nk=9, ell_max=6, n_proj=4, n_seg=3, seed=2, a=1.3, b=0.8),
+    dict(n=(8, 10, 6), nj=9, nk=19, ell_max=8, n_proj=3, n_seg=8, seed=3, two_theta=0.3),
+    dict(n=(5, 5, 5), nj=5, nk=5, ell_max=0, n_proj=6, n_seg=2, seed=4),
+    dict(n=(7, 6, 5), nj=6, nk=7, ell_max=10, n_proj=2, n_seg=6, seed=5),
+    dict(n=(5, 6, 7), nj=8, nk=8, ell_max=12, n_proj=2, n_seg=4, seed=6),
+]
+
+
+@pytest.mark.parametrize("kw", SMALL, ids=lambda kw: f"L{kw['ell_max']}s{kw['seed']}")
+def test_basis_matrix_fp64(kw):
+    st = synth.small_setup(**kw)
+    h = tt.Handle(st, "f32")
+    B = h.basis_matrix().cpu().numpy()
+    np.testing.assert_allclose(B, oracle.basis_matrix(oracle_geometry(st)), atol=1e-13, rtol=0)
+
+
+@pytest.mark.parametrize("kw", SMALL, ids=lambda kw: f"L{kw['ell_max']}s{kw['seed']}")
+def test_project_fp32(kw):
+    st = synth.small_setup(**kw)
+    c = synth.random_volume(st, 10).astype(np.float32)
+    ref = oracle.forward(oracle_geometry(st), c.astype(np.float64))
+    h = tt.Handle(st, "f32")
+    out = h.project(dev(c, torch.float32)).cpu().numpy()
+    assert rel_l2(out, ref) <= F32_TOL
+
+
+@pytest.mark.parametrize("kw", SMALL[:4], ids=lambda kw: f"L{kw['ell_max']}s{kw['seed']}")
+def test_project_and_adjoint_fp64(kw):
+    st = synth.small_setup(**kw)
+    g = oracle_geometry(st)
+    c = synth.random_volume(st, 11)
+    R = synth.random_data(st, 12)
+    h = tt.Handle(st, "f64")
+    assert rel_l2(h.project(dev(c, torch.float64)).cpu().numpy(), oracle.forward(g, c)) <= F64_TOL
+    assert rel_l2(h.adjoint(dev(R, torch.float64)).cpu().numpy(), oracle.adjoint(g, R)) <= F64_TOL
+
+
+@pytest.mark.parametrize("kw", SMALL, ids=lambda kw: f"L{kw['ell_max']}s{kw['seed']}")
+def test_adjoint_fp32(kw):
+    st = synth.small_setup(**kw)
+    R = synth.random_data(st, 13).astype(np.float32)
+    ref = oracle.adjoint(oracle_geometry(st), R.astype(np.float64))
+    h = tt.Handle(st, "f32")
+    out = h.adjoint(dev(R, torch.float32)).cpu().numpy()
+    assert rel_l2(out, ref) <= F32_TOL
+
+
+@pytest.mark.parametrize("kw", SMALL, ids=lambda kw: f"L{kw['ell_max']}s{kw['seed']}")
+@pytest.mark.parametrize("weights", [False, True])
+def test_gradient_residual_fp32(kw, weights):
+    st = synth.small_setup(**kw)
+    c = synth.random_volume(st, 20).astype(np.float32)
+    I = synth.random_data(st, 21).astype(np.float32)
+    W = synth.random_weights(st, 22).astype(np.float32) if weights else None
+    loss_ref, g_ref = oracle.gradient_residual(oracle_geometry(st), c.astype(np.float64), I.astype(np.float64),
+                                               None if W is None else W.astype(np.float64))
+    h = tt.Handle(st, "f32")
+    loss, g = h.gradient_residual(dev(c, torch.float32), dev(I, torch.float32),
+                                  None if W is None else dev(W, torch.float32))
+    assert abs(loss - loss_ref) <= F32_TOL * abs(loss_ref)
+    assert rel_l2(g.cpu().numpy(), g_ref) <= F32_TOL
+
+
+@pytest.mark.parametrize("kw", SMALL[:5], ids=lambda kw: f"L{kw['ell_max']}s{kw['seed']}")
+def test_gradient_residual_fp64(kw):
+    st = synth.small_setup(**kw)
+    c = synth.random_volume(st, 30)
+    I = synth.random_data(st, 31)
+    W = synth.random_weights(st, 32)
+    loss_ref, g_ref = oracle.gradient_residual(oracle_geometry(st), c, I, W)
+    h = tt.Handle(st, "f64")
+    loss, g = h.gradient_residual(dev(c, torch.float64), dev(I, torch.float64), dev(W, torch.float64))
+    assert abs(loss - loss_ref) <= F64_TOL * abs(loss_ref)
+    assert rel_l2(g.cpu().numpy(), g_ref) <= F64_TOL
+
+
+def test_adjoint_identity_on_gpu_fp64():
+    st = synth.small_setup(n=(14, 12, 13), nj=15, nk=17, ell_max=4, n_proj=11, n_seg=6, seed=8)
+    h = tt.Handle(st, "f64")
+    x = dev(synth.random_volume(st, 1), torch.float64)
+    y = dev(synth.random_data(st, 2), torch.float64)
+    lhs = float(torch.sum(h.project(x) * y))
+    rhs = float(torch.sum(x * h.adjoint(y)))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_cylinder_workload_fp64_gradient_and_data():
+    # The FP64 workload: 16^3, l_max 2, 30 projections of 16x16, 8 segments,
+    # cylinder phantom, data = oracle projection + 1% Gaussian noise.
+    st = synth.workload("cyl16")
+    g = oracle_geometry(st)
+    ph = synth.phantom("cyl16")
+    c_true = oracle.zonal_to_sh(2, ph.dirs.reshape(-1, 3), ph.amps.reshape(-1, 2)).reshape(st.volume_shape)
+    I = synth.gaussian_noise(oracle.forward(g, c_true), 0.01, seed=0)
+    h = tt.Handle(st, "f64")
+    assert rel_l2(h.project(dev(c_true, torch.float64)).cpu().numpy(), oracle.forward(g, c_true)) <= F64_TOL
+    c0 = np.zeros(st.volume_shape)
+    for c in (c0, c_true):
+        loss_ref, g_ref = oracle.gradient_residual(g, c, I)
+        loss, gg = h.gradient_residual(dev(c, torch.float64), dev(I, torch.float64))
+        assert abs(loss - loss_ref) <= F64_TOL * loss_ref
+        assert rel_l2(gg.cpu().numpy(), g_ref) <= F64_TOL
+
+
+def test_zonal_to_sh_matches_oracle():
+    rng = np.random.default_rng(0)
+    n = rng.normal(size=(1000, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    for L in (0, 2, 4, 8, 12):
+        a = rng.uniform(0, 1, (1000, L // 2 + 1))
+        ref = oracle.zonal_to_sh(L, n, a)
+        out = tt.zonal_to_sh(L, dev(n, torch.float32), dev(a, torch.float32)).cpu().numpy()
+        np.testing.assert_allclose(out, ref, atol=2e-6 * max(1.0, np.abs(ref).max()))
+
+
+def test_host_entry_point_matches_device_entry_point():
+    st = synth.small_setup(n=(10, 11, 9), nj=12, nk=10, ell_max=4, n_proj=7, n_seg=8, seed=9)
+    c = synth.random_volume(st, 1).astype(np.float32)
+    I = synth.random_data(st, 2).astype(np.float32)
+    W = synth.random_weights(st, 3).astype(np.float32)
+    h = tt.Handle(st, "f32")
+    loss_d, g_d = h.gradient_residual(dev(c, torch.float32), dev(I, torch.float32), dev(W, torch.float32))
+    loss_h, g_h = h.gradient_residual_host(c, I, W)
+    assert loss_h == loss_d
+    np.testing.assert_array_equal(g_h, g_d.cpu().numpy())
+
+
+def test_nonfinite_input_is_reported():
+    st = synth.small_setup(seed=1)
+    c = synth.random_volume(st, 1).astype(np.float32)
+    c[1, 2, 3, 0] = np.nan
+    h = tt.Handle(st, "f32")
+    with pytest.raises(tt.TTError) as e:
+        h.gradient_residual(dev(c, torch.float32), dev(synth.random_data(st, 2), torch.float32))
+    assert e.value.status == tt.TT_NONFINITE
+
+
+def test_precision_mismatch_and_bad_shapes_rejected():
+    st = synth.small_setup(seed=2)
+    h = tt.Handle(st, "f32")
+    lib = tt.load()
+    x = torch.zeros(st.volume_shape, dtype=torch.float64, device="cuda")
+    y = torch.zeros(st.data_shape, dtype=torch.float64, device="cuda")
+    assert lib.tt_project_f64(h._h, x.data_ptr(), y.data_ptr()) == tt.TT_INVALID_ARG
+    x32 = torch.zeros(st.volume_shape, dtype=torch.float32, device="cuda")
+    assert lib.tt_project(h._h, x32.data_ptr() + 4, y.data_ptr()) == tt.TT_INVALID_ARG   # misaligned
+    assert lib.tt_project(h._h, None, y.data_ptr()) == tt.TT_INVALID_ARG
+    with pytest.raises(ValueError):
+        h.project(torch.zeros((3, 3, 3, 6), device="cuda"))
+
+
+def test_degenerate_sizes():
+    # one voxel, one pixel, one projection, one segment
+    st = synth.small_setup(n=(1, 1, 1), nj=1, nk=1, ell_max=2, n_proj=1, n_seg=1, seed=3, offsets=False)
+    c = synth.random_volume(st, 0).astype(np.float32)
+    I = synth.random_data(st, 1).astype(np.float32)
+    loss_ref, g_ref = oracle.gradient_residual(oracle_geometry(st), c.astype(np.float64), I.astype(np.float64))
+    h = tt.Handle(st, "f32")
+    loss, g = h.gradient_residual(dev(c, torch.float32), dev(I, torch.float32))
+    assert abs(loss - loss_ref) <= F32_TOL * abs(loss_ref)
+    assert rel_l2(g.cpu().numpy(), g_ref) <= F32_TOL
+    # a detector that misses the volume entirely: zero projection, zero gradient
+    st2 = synth.small_setup(n=(4, 4, 4), nj=3, nk=3, n_proj=2, seed=4, offsets=False)
+    st2.j_offset[:] = 50.0
+    h2 = tt.Handle(st2, "f32")
+    I2 = dev(synth.random_data(st2, 5), torch.float32)
+    loss2, g2 = h2.gradient_residual(torch.zeros(st2.volume_shape, device="cuda"), I2)
+    assert float(torch.abs(h2.project(dev(synth.random_volume(st2, 1), torch.float32))).max()) == 0.0
+    assert float(torch.abs(g2).max()) == 0.0
+    assert abs(loss2 - float(torch.sum(I2.double() ** 2))) <= 1e-6 * loss2
