@@ -151,6 +151,36 @@ static ProjGeom make_geom(const tt_handle *h, int s)
     return g;
 }
 
+template <typename T>
+static AdjProj<T> adj_proj(const ProjGeom &g)
+{
+    double jc[4] = {g.jc0, 0, 0, 0}, kc[4] = {g.kc0, 0, 0, 0}, bu[4] = {g.u0, 0, 0, 0}, bv[4] = {g.v0, 0, 0, 0};
+    jc[1 + g.m] += g.jP; jc[1 + g.u] += g.jU; jc[1 + g.v] += g.jV;
+    kc[1 + g.m] += g.kP; kc[1 + g.u] += g.kU; kc[1 + g.v] += g.kV;
+    bu[1 + g.m] += g.up; bu[1 + g.u] -= 1.0;
+    bv[1 + g.m] += g.vp; bv[1 + g.v] -= 1.0;
+    AdjProj<T> a;
+    for (int t = 0; t < 4; ++t) { a.jc[t] = (T)jc[t]; a.kc[t] = (T)kc[t]; a.bu[t] = (T)bu[t]; a.bv[t] = (T)bv[t]; }
+    a.uj = (T)g.uj; a.uk = (T)g.uk; a.vj = (T)g.vj; a.vk = (T)g.vk;
+    a.hj = (T)g.hj; a.hk = (T)g.hk; a.step = (T)g.step;
+    a.nwj = g.nwj; a.nwk = g.nwk;
+    a.shape = (g.nwj <= 3 && g.nwk <= 3) ? 16 * g.nwj + g.nwk : 0;
+    return a;
+}
+
+template <typename T>
+static void build_adj_params(const tt_handle *h, std::vector<AdjParams<T>> &out)
+{
+    const int per = AdjParams<T>::kMax;
+    out.assign((h->S + per - 1) / per, AdjParams<T>());
+    for (int s = 0; s < h->S; ++s) out[s / per].p[s % per] = adj_proj<T>(h->geo_host[s]);
+}
+
+template <>
+const std::vector<AdjParams<float>> &adj_params<float>(const tt_handle *h) { return h->adj_f32; }
+template <>
+const std::vector<AdjParams<double>> &adj_params<double>(const tt_handle *h) { return h->adj_f64; }
+
 // Gauss-Legendre nodes/weights on [-1, 1] (Newton on the three-term recurrence).
 static void gauss_legendre(int n, double *x, double *w)
 {
@@ -259,8 +289,7 @@ static tt_status adjoint_impl(tt_handle *h, const T *R, T *g)
 {
     if (bad_ptr(R) || bad_ptr(g)) return invalid("tt_adjoint: device pointers must be non-null and 16-byte aligned");
     TT_CUDA(launch_backcontract<T>(h, R, (T *)h->G), "backcontract");
-    TT_CUDA(launch_adjoint<T>(h, (const T *)h->G, (T *)h->gpad), "adjoint");
-    TT_CUDA(launch_unpack<T>(h, (const T *)h->gpad, g), "unpack");
+    TT_CUDA(launch_adjoint<T>(h, (const T *)h->G, g), "adjoint");
     return TT_OK;
 }
 
@@ -277,10 +306,7 @@ tt_status tt_grad_enqueue(tt_handle *h, const T *c, const T *I, const T *W, T *g
     TT_CUDA(launch_pack<T>(h, c, (T *)h->cpad), "pack");
     TT_CUDA(launch_forward<T>(h, (const T *)h->cpad, nullptr, I, W, true), "forward");
     TT_CUDA(launch_reduce(h, h->partials, h->n_partials, h->loss_dev, nullptr, 1.0), "loss reduce");
-    if (g) {
-        TT_CUDA(launch_adjoint<T>(h, (const T *)h->G, (T *)h->gpad), "adjoint");
-        TT_CUDA(launch_unpack<T>(h, (const T *)h->gpad, g), "unpack");
-    }
+    if (g) TT_CUDA(launch_adjoint<T>(h, (const T *)h->G, g), "adjoint");
     return TT_OK;
 }
 template tt_status tt_grad_enqueue<float>(tt_handle *, const float *, const float *, const float *, float *);
@@ -369,6 +395,8 @@ tt_status tt_create(const tt_problem *P, tt_precision prec, void *stream, tt_han
     h->seg1.assign(P->seg_end, P->seg_end + h->C);
     h->geo_host.resize(h->S);
     for (int s = 0; s < h->S; ++s) h->geo_host[s] = make_geom(h, s);
+    if (prec == TT_F32) build_adj_params<float>(h, h->adj_f32);
+    else build_adj_params<double>(h, h->adj_f64);
 
     const size_t es = h->esize();
 #define ALLOC(ptr, bytes)                                                     \

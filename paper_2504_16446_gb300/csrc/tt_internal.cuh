@@ -48,6 +48,26 @@ struct ProjGeom {
     int nwj, nwk;
 };
 
+// Per-projection constants of the adjoint gather in the element type, as
+// affine functions of the voxel indices (x, y, z):
+//   jc = jc[0] + jc[1] x + jc[2] y + jc[3] z        (likewise kc)
+//   du(j,k) = bu(x,y,z) + j uj + k uk,  dv(j,k) = bv(x,y,z) + j vj + k vk
+// shape = 16 * nwj + nwk (window of candidate rays).
+template <typename T>
+struct AdjProj {
+    T jc[4], kc[4], bu[4], bv[4];
+    T uj, uk, vj, vk, hj, hk, step;
+    int shape, nwj, nwk;
+};
+
+// Kernel-parameter block holding the constants of up to kMax projections
+// (kept under the 32 KB kernel-parameter limit).
+template <typename T>
+struct AdjParams {
+    static constexpr int kMax = sizeof(T) == 4 ? 256 : 128;
+    AdjProj<T> p[kMax];
+};
+
 struct Profile {
     bool enabled = false;
     std::vector<cudaEvent_t> pool;     // recorded pairs awaiting read
@@ -83,6 +103,8 @@ struct tt_handle {
     void *hc = nullptr, *hI = nullptr, *hW = nullptr, *hg = nullptr;
     long long launch_count = 0;
     tt::Profile prof;
+    std::vector<tt::AdjParams<float>> adj_f32;     // adjoint constants, one block per launch
+    std::vector<tt::AdjParams<double>> adj_f64;
 
     long long nvox() const { return (long long)N[0] * N[1] * N[2]; }
     long long npix() const { return (long long)S * nj * nk; }
@@ -94,6 +116,13 @@ namespace tt {
 
 void set_error(const std::string &msg);
 tt_status cuda_fail(cudaError_t e, const char *what);
+
+template <typename T>
+const std::vector<AdjParams<T>> &adj_params(const tt_handle *h);
+template <>
+const std::vector<AdjParams<float>> &adj_params<float>(const tt_handle *h);
+template <>
+const std::vector<AdjParams<double>> &adj_params<double>(const tt_handle *h);
 
 // Bracket a kernel launch with the handle's profiling events.
 void prof_begin(tt_handle *h, int slot, cudaEvent_t *ev);
@@ -108,8 +137,10 @@ template <typename T>
 cudaError_t launch_forward(tt_handle *h, const T *cpad, T *Iout, const T *I, const T *W, bool grad);
 template <typename T>
 cudaError_t launch_backcontract(tt_handle *h, const T *R, T *G);
+// g [nvox][K] (unpadded) = exact-transpose gather of G; S above one
+// parameter block runs several launches accumulating in h->gpad.
 template <typename T>
-cudaError_t launch_adjoint(tt_handle *h, const T *G, T *gpad);
+cudaError_t launch_adjoint(tt_handle *h, const T *G, T *g);
 cudaError_t launch_reduce(tt_handle *h, const double *partials, long long n, double *out,
                           const double *add, double mul);
 cudaError_t launch_basis(tt_handle *h, const double *nodes, const double *weights);

@@ -12,6 +12,9 @@
 // vector loads.
 #pragma once
 
+#include <algorithm>
+#include <vector>
+
 #include "tt_internal.cuh"
 
 namespace tt {
@@ -280,81 +283,114 @@ __device__ __forceinline__ int sel3(int x, int y, int z, int axis)
 // (|u - U| < 1 and |v - V| < 1, weight (1-|du|)(1-|dv|) * step, the same
 // weight the forward gave this tap) and accumulates their G rows.  Every
 // voxel is written once; no atomics.
-template <typename T>
-struct AdjConst {
-    T jc0, jU, jV, jP, kc0, kU, kV, kP, hj, hk;
-    T u0, up, uj, uk, v0, vp, vj, vk, step;
-    int m, u, v, nwj, nwk;
-};
+//
+// The candidate rays of voxel (x,y,z) form the integer points of a window of
+// nwj x nwk pixels starting at (floor(jc - hj) + 1, floor(kc - hk) + 1); the
+// window shape is uniform per projection, so the candidate loop is unrolled
+// per shape.  Per-projection constants travel in the kernel's parameter
+// space (one copy per launch, read through the constant cache).
+template <typename T, int CPL, int KP, int NJ, int NK>
+__device__ __forceinline__ void adj_window(T (&acc)[CPL], const T *__restrict__ row0, int nk, T du0, T dv0,
+                                           const AdjProj<T> &c, unsigned jmask, unsigned kmask)
+{
+#pragma unroll
+    for (int a = 0; a < NJ; ++a) {
+#pragma unroll
+        for (int b = 0; b < NK; ++b) {
+            const T du = du0 + (T)a * c.uj + (T)b * c.uk;
+            const T dv = dv0 + (T)a * c.vj + (T)b * c.vk;
+            const T tu = T(1) - fabs(du);
+            const T tv = c.step - c.step * fabs(dv);
+            if (((jmask >> a) & (kmask >> b) & 1u) && tu > T(0) && tv > T(0))
+                fma_row<T, CPL>(acc, tu * tv, row0 + ((long long)a * nk + b) * KP);
+        }
+    }
+}
 
-constexpr int kAdjChunk = 128;   // projections staged in shared memory at a time
+template <typename T, int CPL, int KP>
+__device__ __noinline__ void adj_window_any(T (&acc)[CPL], const T *__restrict__ row0, int nj, int nk, int j0,
+                                            int k0, T du0, T dv0, const AdjProj<T> &c)
+{
+    for (int a = 0; a < c.nwj; ++a) {
+        if ((unsigned)(j0 + a) >= (unsigned)nj) continue;
+        for (int b = 0; b < c.nwk; ++b) {
+            if ((unsigned)(k0 + b) >= (unsigned)nk) continue;
+            const T du = du0 + (T)a * c.uj + (T)b * c.uk;
+            const T dv = dv0 + (T)a * c.vj + (T)b * c.vk;
+            const T tu = T(1) - fabs(du);
+            const T tv = c.step - c.step * fabs(dv);
+            if (tu > T(0) && tv > T(0)) fma_row<T, CPL>(acc, tu * tv, row0 + ((long long)a * nk + b) * KP);
+        }
+    }
+}
 
 template <typename T, int KP, int LG>
 __global__ void __launch_bounds__(kThreads)
-k_adjoint(const ProjGeom *__restrict__ geo, int S, const T *__restrict__ G, int nj, int nk,
-          int nx, int ny, int nz, int ty, int tz, T *__restrict__ gpad)
+k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const T *__restrict__ G, int nj, int nk, int nx,
+          int ny, int nz, int ty, int tz, T *__restrict__ gpad, int accumulate, T *__restrict__ gout, int K)
 {
     constexpr int CPL = KP / LG;
     constexpr int VOX = kThreads / LG;
     constexpr int BZ = 4, BY = 4, BX = VOX / 16;
-    __shared__ AdjConst<T> cs[kAdjChunk];
 
     const int b = blockIdx.x;
     const int bz = b % tz, by = (b / tz) % ty, bx = b / (tz * ty);
     const int r = threadIdx.x / LG, q = threadIdx.x % LG;
     const int x = bx * BX + r / (BY * BZ), y = by * BY + (r / BZ) % BY, z = bz * BZ + r % BZ;
     const bool valid = (x < nx) && (y < ny) && (z < nz);
+    const T fx = (T)x, fy = (T)y, fz = (T)z;
 
     T acc[CPL];
 #pragma unroll
     for (int i = 0; i < CPL; ++i) acc[i] = T(0);
     const size_t gstride = (size_t)nj * nk * KP;
+    const T *Gq = G + q * CPL;
 
-    for (int s0 = 0; s0 < S; s0 += kAdjChunk) {
-        const int ns = min(kAdjChunk, S - s0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < ns; t += kThreads) {
-            const ProjGeom &P = geo[s0 + t];
-            AdjConst<T> c;
-            c.jc0 = (T)P.jc0; c.jU = (T)P.jU; c.jV = (T)P.jV; c.jP = (T)P.jP;
-            c.kc0 = (T)P.kc0; c.kU = (T)P.kU; c.kV = (T)P.kV; c.kP = (T)P.kP;
-            c.hj = (T)P.hj; c.hk = (T)P.hk;
-            c.u0 = (T)P.u0; c.up = (T)P.up; c.uj = (T)P.uj; c.uk = (T)P.uk;
-            c.v0 = (T)P.v0; c.vp = (T)P.vp; c.vj = (T)P.vj; c.vk = (T)P.vk;
-            c.step = (T)P.step;
-            c.m = P.m; c.u = P.u; c.v = P.v; c.nwj = P.nwj; c.nwk = P.nwk;
-            cs[t] = c;
-        }
-        __syncthreads();
+    if (valid) {
         for (int si = 0; si < ns; ++si) {
-            const AdjConst<T> &c = cs[si];
-            const T fp = (T)sel3(x, y, z, c.m), fU = (T)sel3(x, y, z, c.u), fV = (T)sel3(x, y, z, c.v);
-            const T jc = c.jc0 + c.jU * fU + c.jV * fV + c.jP * fp;
-            const T kc = c.kc0 + c.kU * fU + c.kV * fV + c.kP * fp;
-            const T bu = (c.u0 - fU) + c.up * fp, bv = (c.v0 - fV) + c.vp * fp;
-            const int j0 = (int)floor(jc - c.hj) + 1, k0 = (int)floor(kc - c.hk) + 1;
-            const T *Gs = G + (size_t)(s0 + si) * gstride + q * CPL;
-            for (int a = 0; a < c.nwj; ++a) {
-                const int jj = j0 + a;
-                T du = bu + (T)jj * c.uj + (T)k0 * c.uk;
-                T dv = bv + (T)jj * c.vj + (T)k0 * c.vk;
-                for (int bb = 0; bb < c.nwk; ++bb) {
-                    const int kk = k0 + bb;
-                    const T adu = fabs(du), adv = fabs(dv);
-                    if (valid && adu < T(1) && adv < T(1) && (unsigned)jj < (unsigned)nj &&
-                        (unsigned)kk < (unsigned)nk) {
-                        const T w = (T(1) - adu) * (T(1) - adv) * c.step;
-                        fma_row<T, CPL>(acc, w, Gs + ((size_t)jj * nk + kk) * KP);
-                    }
-                    du += c.uk;
-                    dv += c.vk;
-                }
+            const AdjProj<T> &c = P.p[si];
+            const T jc = c.jc[0] + c.jc[1] * fx + c.jc[2] * fy + c.jc[3] * fz;
+            const T kc = c.kc[0] + c.kc[1] * fx + c.kc[2] * fy + c.kc[3] * fz;
+            const T bu = c.bu[0] + c.bu[1] * fx + c.bu[2] * fy + c.bu[3] * fz;
+            const T bv = c.bv[0] + c.bv[1] * fx + c.bv[2] * fy + c.bv[3] * fz;
+            const T fj = floor(jc - c.hj) + T(1), fk = floor(kc - c.hk) + T(1);
+            const int j0 = (int)fj, k0 = (int)fk;
+            const T du0 = bu + fj * c.uj + fk * c.uk;
+            const T dv0 = bv + fj * c.vj + fk * c.vk;
+            const T *row0 = Gq + (size_t)si * gstride + ((long long)j0 * nk + k0) * KP;
+            unsigned jm = 0, km = 0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                jm |= (unsigned)((unsigned)(j0 + a) < (unsigned)nj) << a;
+                km |= (unsigned)((unsigned)(k0 + a) < (unsigned)nk) << a;
+            }
+            switch (c.shape) {
+            case 0x11: adj_window<T, CPL, KP, 1, 1>(acc, row0, nk, du0, dv0, c, jm, km); break;
+            case 0x12: adj_window<T, CPL, KP, 1, 2>(acc, row0, nk, du0, dv0, c, jm, km); break;
+            case 0x13: adj_window<T, CPL, KP, 1, 3>(acc, row0, nk, du0, dv0, c, jm, km); break;
+            case 0x21: adj_window<T, CPL, KP, 2, 1>(acc, row0, nk, du0, dv0, c, jm, km); break;
+            case 0x22: adj_window<T, CPL, KP, 2, 2>(acc, row0, nk, du0, dv0, c, jm, km); break;
+            case 0x23: adj_window<T, CPL, KP, 2, 3>(acc, row0, nk, du0, dv0, c, jm, km); break;
+            case 0x31: adj_window<T, CPL, KP, 3, 1>(acc, row0, nk, du0, dv0, c, jm, km); break;
+            case 0x32: adj_window<T, CPL, KP, 3, 2>(acc, row0, nk, du0, dv0, c, jm, km); break;
+            case 0x33: adj_window<T, CPL, KP, 3, 3>(acc, row0, nk, du0, dv0, c, jm, km); break;
+            default: adj_window_any<T, CPL, KP>(acc, row0, nj, nk, j0, k0, du0, dv0, c); break;
             }
         }
-    }
-    if (valid) {
         const long long vox = ((long long)x * ny + y) * nz + z;
-        store_row<T, CPL>(gpad + vox * KP + q * CPL, acc, T(1));
+        if (accumulate) {
+            const T *prev = gpad + vox * KP + q * CPL;
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) acc[i] += prev[i];
+        }
+        if (gout) {
+            T *o = gout + vox * K;
+#pragma unroll
+            for (int i = 0; i < CPL; ++i)
+                if (q * CPL + i < K) o[q * CPL + i] = acc[i];
+        } else {
+            store_row<T, CPL>(gpad + vox * KP + q * CPL, acc, T(1));
+        }
     }
 }
 
@@ -404,17 +440,26 @@ cudaError_t launch_backcontract_L(tt_handle *h, const T *R, T *G)
 }
 
 template <typename T, int L>
-cudaError_t launch_adjoint_L(tt_handle *h, const T *G, T *gpad)
+cudaError_t launch_adjoint_L(tt_handle *h, const T *G, T *g)
 {
     constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K);
     constexpr int VOX = kThreads / LG, BZ = 4, BY = 4, BX = VOX / 16;
     const int tx = (h->N[0] + BX - 1) / BX, ty = (h->N[1] + BY - 1) / BY, tz = (h->N[2] + BZ - 1) / BZ;
-    cudaEvent_t ev;
-    prof_begin(h, TT_KSLOT_ADJOINT, &ev);
-    k_adjoint<T, KP, LG><<<(unsigned)(tx * ty * tz), kThreads, 0, h->stream>>>(
-        h->geo, h->S, G, h->nj, h->nk, h->N[0], h->N[1], h->N[2], ty, tz, gpad);
-    cudaError_t e = cudaGetLastError();
-    prof_end(h, TT_KSLOT_ADJOINT, ev);
+    const std::vector<AdjParams<T>> &chunks = adj_params<T>(h);
+    cudaError_t e = cudaSuccess;
+    const int nchunk = (int)chunks.size();
+    for (int ci = 0; ci < nchunk && e == cudaSuccess; ++ci) {
+        const int s0 = ci * AdjParams<T>::kMax;
+        const int ns = std::min(AdjParams<T>::kMax, h->S - s0);
+        const bool last = ci == nchunk - 1;
+        cudaEvent_t ev;
+        prof_begin(h, TT_KSLOT_ADJOINT, &ev);
+        k_adjoint<T, KP, LG><<<(unsigned)(tx * ty * tz), kThreads, 0, h->stream>>>(
+            chunks[ci], ns, G + (size_t)s0 * h->nj * h->nk * KP, h->nj, h->nk, h->N[0], h->N[1], h->N[2], ty, tz,
+            (T *)h->gpad, ci > 0 ? 1 : 0, last ? g : nullptr, h->K);
+        e = cudaGetLastError();
+        prof_end(h, TT_KSLOT_ADJOINT, ev);
+    }
     return e;
 }
 

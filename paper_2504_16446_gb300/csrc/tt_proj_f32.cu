@@ -20,9 +20,9 @@ cudaError_t launch_backcontract<float>(tt_handle *h, const float *R, float *G)
 }
 
 template <>
-cudaError_t launch_adjoint<float>(tt_handle *h, const float *G, float *gpad)
+cudaError_t launch_adjoint<float>(tt_handle *h, const float *G, float *g)
 {
-#define TT_CALL(L) launch_adjoint_L<float, L>(h, G, gpad)
+#define TT_CALL(L) launch_adjoint_L<float, L>(h, G, g)
     TT_DISPATCH_L(h->L, TT_CALL)
 #undef TT_CALL
 }

@@ -20,9 +20,9 @@ cudaError_t launch_backcontract<double>(tt_handle *h, const double *R, double *G
 }
 
 template <>
-cudaError_t launch_adjoint<double>(tt_handle *h, const double *G, double *gpad)
+cudaError_t launch_adjoint<double>(tt_handle *h, const double *G, double *g)
 {
-#define TT_CALL(L) launch_adjoint_L<double, L>(h, G, gpad)
+#define TT_CALL(L) launch_adjoint_L<double, L>(h, G, g)
     TT_DISPATCH_L(h->L, TT_CALL)
 #undef TT_CALL
 }

@@ -275,9 +275,9 @@ def random_weights(setup: Setup, seed: int, zero_frac: float = 0.1, dtype=np.flo
 
 
 def gaussian_noise(clean: np.ndarray, rel_sigma: float, seed: int) -> np.ndarray:
-    """clean + N(0, (rel_sigma * mean(clean))^2)."""
+    """clean + N(0, (rel_sigma * mean|clean|)^2)."""
     rng = np.random.default_rng(seed)
-    return clean + rng.normal(scale=rel_sigma * float(np.mean(clean)), size=clean.shape)
+    return clean + rng.normal(scale=rel_sigma * float(np.mean(np.abs(clean))), size=clean.shape)
 
 
 def poisson_counts(clean: np.ndarray, mean_counts: float, seed: int) -> np.ndarray:
