@@ -277,21 +277,25 @@ __device__ __forceinline__ int sel3(int x, int y, int z, int axis)
 
 // ---------------------------------------------------------- adjoint kernel
 //
-// Exact transpose of k_forward's Joseph discretisation, as a gather: one lane
-// group per voxel, looping over all projections; on the voxel's plane of
-// projection s it visits the rays whose bilinear footprint contains the voxel
-// (|u - U| < 1 and |v - V| < 1, weight (1-|du|)(1-|dv|) * step, the same
-// weight the forward gave this tap) and accumulates their G rows.  Every
-// voxel is written once; no atomics.
+// Exact transpose of k_forward's Joseph discretisation, as a gather (every
+// voxel written once, no atomics).  On the voxel's plane of projection s, the
+// rays that have voxel (U,V) as a bilinear tap are those with |u - U| < 1 and
+// |v - V| < 1; each contributes its G row with weight (1-|du|)(1-|dv|) *
+// step, the weight the forward gave that tap.  Those rays are integer points
+// of a window of nwj x nwk pixels starting at (floor(jc - hj) + 1,
+// floor(kc - hk) + 1); the window shape is uniform per projection, so the
+// candidate loop is unrolled per shape.
 //
-// The candidate rays of voxel (x,y,z) form the integer points of a window of
-// nwj x nwk pixels starting at (floor(jc - hj) + 1, floor(kc - hk) + 1); the
-// window shape is uniform per projection, so the candidate loop is unrolled
-// per shape.  Per-projection constants travel in the kernel's parameter
-// space (one copy per launch, read through the constant cache).
-template <typename T, int CPL, int KP, int NJ, int NK>
-__device__ __forceinline__ void adj_window(T (&acc)[CPL], const T *__restrict__ row0, int nk, T du0, T dv0,
-                                           const AdjProj<T> &c, unsigned jmask, unsigned kmask)
+// Work split: a lane group of LG lanes owns LG voxels (consecutive in z).
+// Lane q does the candidate geometry for voxel q only, then the group
+// broadcasts each candidate's (row, weight) with shuffles and every lane
+// accumulates its own channel chunk q of that row for all LG voxels.  The
+// geometry is thus computed once per voxel while a G row is still read as
+// one contiguous KP-float segment by the LG lanes together.  Per-projection
+// constants travel in the kernel's parameter space.
+template <typename T, int CPL, int KP, int LG, int NJ, int NK>
+__device__ __forceinline__ void adj_window(T (&acc)[LG][CPL], const T *__restrict__ Gq, int nk, int r0, T du0,
+                                           T dv0, const AdjProj<T> &c, unsigned jmask, unsigned kmask)
 {
 #pragma unroll
     for (int a = 0; a < NJ; ++a) {
@@ -301,25 +305,39 @@ __device__ __forceinline__ void adj_window(T (&acc)[CPL], const T *__restrict__ 
             const T dv = dv0 + (T)a * c.vj + (T)b * c.vk;
             const T tu = T(1) - fabs(du);
             const T tv = c.step - c.step * fabs(dv);
-            if (((jmask >> a) & (kmask >> b) & 1u) && tu > T(0) && tv > T(0))
-                fma_row<T, CPL>(acc, tu * tv, row0 + ((long long)a * nk + b) * KP);
+            const bool hit = ((jmask >> a) & (kmask >> b) & 1u) && tu > T(0) && tv > T(0);
+            const T w = hit ? tu * tv : T(0);
+            const int row = r0 + a * nk + b;
+#pragma unroll
+            for (int src = 0; src < LG; ++src) {
+                const T ws = (LG == 1) ? w : __shfl_sync(0xffffffffu, w, src, LG);
+                const int rs = (LG == 1) ? row : __shfl_sync(0xffffffffu, row, src, LG);
+                if (ws != T(0)) fma_row<T, CPL>(acc[src], ws, Gq + (long long)rs * KP);
+            }
         }
     }
 }
 
-template <typename T, int CPL, int KP>
-__device__ __noinline__ void adj_window_any(T (&acc)[CPL], const T *__restrict__ row0, int nj, int nk, int j0,
-                                            int k0, T du0, T dv0, const AdjProj<T> &c)
+template <typename T, int CPL, int KP, int LG>
+__device__ __forceinline__ void adj_window_any(T (&acc)[LG][CPL], const T *__restrict__ Gq, int nj, int nk, int j0,
+                                            int k0, T du0, T dv0, const AdjProj<T> &c, bool valid)
 {
     for (int a = 0; a < c.nwj; ++a) {
-        if ((unsigned)(j0 + a) >= (unsigned)nj) continue;
         for (int b = 0; b < c.nwk; ++b) {
-            if ((unsigned)(k0 + b) >= (unsigned)nk) continue;
             const T du = du0 + (T)a * c.uj + (T)b * c.uk;
             const T dv = dv0 + (T)a * c.vj + (T)b * c.vk;
             const T tu = T(1) - fabs(du);
             const T tv = c.step - c.step * fabs(dv);
-            if (tu > T(0) && tv > T(0)) fma_row<T, CPL>(acc, tu * tv, row0 + ((long long)a * nk + b) * KP);
+            const bool hit = valid && (unsigned)(j0 + a) < (unsigned)nj && (unsigned)(k0 + b) < (unsigned)nk &&
+                             tu > T(0) && tv > T(0);
+            const T w = hit ? tu * tv : T(0);
+            const int row = (j0 + a) * nk + (k0 + b);
+#pragma unroll
+            for (int src = 0; src < LG; ++src) {
+                const T ws = (LG == 1) ? w : __shfl_sync(0xffffffffu, w, src, LG);
+                const int rs = (LG == 1) ? row : __shfl_sync(0xffffffffu, row, src, LG);
+                if (ws != T(0)) fma_row<T, CPL>(acc[src], ws, Gq + (long long)rs * KP);
+            }
         }
     }
 }
@@ -330,23 +348,30 @@ k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const T *__restrict__ 
           int ny, int nz, int ty, int tz, T *__restrict__ gpad, int accumulate, T *__restrict__ gout, int K)
 {
     constexpr int CPL = KP / LG;
-    constexpr int VOX = kThreads / LG;
-    constexpr int BZ = 4, BY = 4, BX = VOX / 16;
+    // CTA box: 4 (x) x 8 (y) x (8 LG... ) voxels; a lane group covers LG consecutive z
+    constexpr int GROUPS = kThreads / LG;          // lane groups per CTA
+    constexpr int BZ = 4 * LG, BY = 4, BX = (GROUPS * LG) / (BZ * BY);
 
     const int b = blockIdx.x;
     const int bz = b % tz, by = (b / tz) % ty, bx = b / (tz * ty);
-    const int r = threadIdx.x / LG, q = threadIdx.x % LG;
-    const int x = bx * BX + r / (BY * BZ), y = by * BY + (r / BZ) % BY, z = bz * BZ + r % BZ;
+    const int g = threadIdx.x / LG, q = threadIdx.x % LG;
+    const int zg = (g % (BZ / LG)) * LG;            // first z of the group within the box
+    const int yl = (g / (BZ / LG)) % BY, xl = g / ((BZ / LG) * BY);
+    const int x = bx * BX + xl, y = by * BY + yl, z0 = bz * BZ + zg;
+    const int z = z0 + q;                           // this lane's own voxel for the geometry
     const bool valid = (x < nx) && (y < ny) && (z < nz);
     const T fx = (T)x, fy = (T)y, fz = (T)z;
 
-    T acc[CPL];
+    T acc[LG][CPL];
 #pragma unroll
-    for (int i = 0; i < CPL; ++i) acc[i] = T(0);
+    for (int v = 0; v < LG; ++v)
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) acc[v][i] = T(0);
     const size_t gstride = (size_t)nj * nk * KP;
-    const T *Gq = G + q * CPL;
 
-    if (valid) {
+    // Lane groups whose voxels all lie outside the volume skip the loop as a whole.
+    const bool group_live = (x < nx) && (y < ny) && (z0 < nz);
+    if (group_live) {
         for (int si = 0; si < ns; ++si) {
             const AdjProj<T> &c = P.p[si];
             const T jc = c.jc[0] + c.jc[1] * fx + c.jc[2] * fy + c.jc[3] * fz;
@@ -357,39 +382,47 @@ k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const T *__restrict__ 
             const int j0 = (int)fj, k0 = (int)fk;
             const T du0 = bu + fj * c.uj + fk * c.uk;
             const T dv0 = bv + fj * c.vj + fk * c.vk;
-            const T *row0 = Gq + (size_t)si * gstride + ((long long)j0 * nk + k0) * KP;
+            const int r0 = j0 * nk + k0;
             unsigned jm = 0, km = 0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 jm |= (unsigned)((unsigned)(j0 + a) < (unsigned)nj) << a;
                 km |= (unsigned)((unsigned)(k0 + a) < (unsigned)nk) << a;
             }
+            if (!valid) { jm = 0; km = 0; }
+            const T *Gq = G + (size_t)si * gstride + q * CPL;
             switch (c.shape) {
-            case 0x11: adj_window<T, CPL, KP, 1, 1>(acc, row0, nk, du0, dv0, c, jm, km); break;
-            case 0x12: adj_window<T, CPL, KP, 1, 2>(acc, row0, nk, du0, dv0, c, jm, km); break;
-            case 0x13: adj_window<T, CPL, KP, 1, 3>(acc, row0, nk, du0, dv0, c, jm, km); break;
-            case 0x21: adj_window<T, CPL, KP, 2, 1>(acc, row0, nk, du0, dv0, c, jm, km); break;
-            case 0x22: adj_window<T, CPL, KP, 2, 2>(acc, row0, nk, du0, dv0, c, jm, km); break;
-            case 0x23: adj_window<T, CPL, KP, 2, 3>(acc, row0, nk, du0, dv0, c, jm, km); break;
-            case 0x31: adj_window<T, CPL, KP, 3, 1>(acc, row0, nk, du0, dv0, c, jm, km); break;
-            case 0x32: adj_window<T, CPL, KP, 3, 2>(acc, row0, nk, du0, dv0, c, jm, km); break;
-            case 0x33: adj_window<T, CPL, KP, 3, 3>(acc, row0, nk, du0, dv0, c, jm, km); break;
-            default: adj_window_any<T, CPL, KP>(acc, row0, nj, nk, j0, k0, du0, dv0, c); break;
+            case 0x11: adj_window<T, CPL, KP, LG, 1, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x12: adj_window<T, CPL, KP, LG, 1, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x13: adj_window<T, CPL, KP, LG, 1, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x21: adj_window<T, CPL, KP, LG, 2, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x22: adj_window<T, CPL, KP, LG, 2, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x23: adj_window<T, CPL, KP, LG, 2, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x31: adj_window<T, CPL, KP, LG, 3, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x32: adj_window<T, CPL, KP, LG, 3, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x33: adj_window<T, CPL, KP, LG, 3, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            default: adj_window_any<T, CPL, KP, LG>(acc, Gq, nj, nk, j0, k0, du0, dv0, c, valid); break;
             }
         }
-        const long long vox = ((long long)x * ny + y) * nz + z;
+    }
+    // lane q writes channel chunk q of the group's LG voxels
+#pragma unroll
+    for (int v = 0; v < LG; ++v) {
+        const int zv = z0 + v;
+        if (!(x < nx && y < ny && zv < nz)) continue;
+        const long long vox = ((long long)x * ny + y) * nz + zv;
         if (accumulate) {
             const T *prev = gpad + vox * KP + q * CPL;
 #pragma unroll
-            for (int i = 0; i < CPL; ++i) acc[i] += prev[i];
+            for (int i = 0; i < CPL; ++i) acc[v][i] += prev[i];
         }
         if (gout) {
             T *o = gout + vox * K;
 #pragma unroll
             for (int i = 0; i < CPL; ++i)
-                if (q * CPL + i < K) o[q * CPL + i] = acc[i];
+                if (q * CPL + i < K) o[q * CPL + i] = acc[v][i];
         } else {
-            store_row<T, CPL>(gpad + vox * KP + q * CPL, acc, T(1));
+            store_row<T, CPL>(gpad + vox * KP + q * CPL, acc[v], T(1));
         }
     }
 }
@@ -443,7 +476,7 @@ template <typename T, int L>
 cudaError_t launch_adjoint_L(tt_handle *h, const T *G, T *g)
 {
     constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K);
-    constexpr int VOX = kThreads / LG, BZ = 4, BY = 4, BX = VOX / 16;
+    constexpr int GROUPS = kThreads / LG, BZ = 4 * LG, BY = 4, BX = (GROUPS * LG) / (BZ * BY);
     const int tx = (h->N[0] + BX - 1) / BX, ty = (h->N[1] + BY - 1) / BY, tz = (h->N[2] + BZ - 1) / BZ;
     const std::vector<AdjParams<T>> &chunks = adj_params<T>(h);
     cudaError_t e = cudaSuccess;
