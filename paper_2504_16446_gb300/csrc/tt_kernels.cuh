@@ -343,22 +343,24 @@ __device__ __forceinline__ void adj_window_any(T (&acc)[LG][CPL], const T *__res
 }
 
 template <typename T, int KP, int LG>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const T *__restrict__ G, int nj, int nk, int nx,
           int ny, int nz, int ty, int tz, T *__restrict__ gpad, int accumulate, T *__restrict__ gout, int K)
 {
     constexpr int CPL = KP / LG;
-    // CTA box: 4 (x) x 8 (y) x (8 LG... ) voxels; a lane group covers LG consecutive z
-    constexpr int GROUPS = kThreads / LG;          // lane groups per CTA
-    constexpr int BZ = 4 * LG, BY = 4, BX = (GROUPS * LG) / (BZ * BY);
+    // A warp's 32/LG lane groups take consecutive z, and lane q of a group
+    // owns the voxel (32/LG) * q further along z, so that the rows the warp
+    // reads for one broadcast source are rays of neighbouring voxels.
+    constexpr int GPW = 32 / LG;                   // lane groups per warp
+    constexpr int BZ = 32, BY = 4, BX = (kThreads / 32) / BY;
 
     const int b = blockIdx.x;
     const int bz = b % tz, by = (b / tz) % ty, bx = b / (tz * ty);
-    const int g = threadIdx.x / LG, q = threadIdx.x % LG;
-    const int zg = (g % (BZ / LG)) * LG;            // first z of the group within the box
-    const int yl = (g / (BZ / LG)) % BY, xl = g / ((BZ / LG) * BY);
-    const int x = bx * BX + xl, y = by * BY + yl, z0 = bz * BZ + zg;
-    const int z = z0 + q;                           // this lane's own voxel for the geometry
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = lane / LG, q = lane % LG;
+    const int x = bx * BX + warp / BY, y = by * BY + warp % BY;
+    const int z0 = bz * BZ + gw;                   // voxel of source v is z0 + GPW * v
+    const int z = z0 + GPW * q;
     const bool valid = (x < nx) && (y < ny) && (z < nz);
     const T fx = (T)x, fy = (T)y, fz = (T)z;
 
@@ -369,8 +371,8 @@ k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const T *__restrict__ 
         for (int i = 0; i < CPL; ++i) acc[v][i] = T(0);
     const size_t gstride = (size_t)nj * nk * KP;
 
-    // Lane groups whose voxels all lie outside the volume skip the loop as a whole.
-    const bool group_live = (x < nx) && (y < ny) && (z0 < nz);
+    // Warps whose voxels all lie outside the volume skip the loop as a whole.
+    const bool group_live = (x < nx) && (y < ny) && (bz * BZ < nz);
     if (group_live) {
         for (int si = 0; si < ns; ++si) {
             const AdjProj<T> &c = P.p[si];
@@ -408,7 +410,7 @@ k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const T *__restrict__ 
     // lane q writes channel chunk q of the group's LG voxels
 #pragma unroll
     for (int v = 0; v < LG; ++v) {
-        const int zv = z0 + v;
+        const int zv = z0 + GPW * v;
         if (!(x < nx && y < ny && zv < nz)) continue;
         const long long vox = ((long long)x * ny + y) * nz + zv;
         if (accumulate) {
@@ -476,7 +478,7 @@ template <typename T, int L>
 cudaError_t launch_adjoint_L(tt_handle *h, const T *G, T *g)
 {
     constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K);
-    constexpr int GROUPS = kThreads / LG, BZ = 4 * LG, BY = 4, BX = (GROUPS * LG) / (BZ * BY);
+    constexpr int BZ = 32, BY = 4, BX = (kThreads / 32) / BY;
     const int tx = (h->N[0] + BX - 1) / BX, ty = (h->N[1] + BY - 1) / BY, tz = (h->N[2] + BZ - 1) / BZ;
     const std::vector<AdjParams<T>> &chunks = adj_params<T>(h);
     cudaError_t e = cudaSuccess;
