@@ -114,6 +114,25 @@ tt_status tt_get_sizes(const tt_handle *h, int *K, int *K_padded, long long *n_v
  * (device, [n_proj][n_seg][K] doubles). */
 tt_status tt_basis_matrix(tt_handle *h, double *B_dev);
 
+/* The basis matrix of tt_basis_matrix without a handle and without allocating
+ * device memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc -- e.g. a process whose device memory is
+ * owned and pre-reserved by another allocator, or code that must not trigger
+ * the implicit device synchronisation of cudaMalloc/cudaFree.  Its scratch
+ * (quadrature rule, rotated frames, segment bounds) is a fixed file-scope
+ * device array of 18,624 doubles (145.5 KiB), present on every device that
+ * loads libtt until the process exits; hence n_proj <= 2048 (n_seg <= 64,
+ * ell_max <= 12 as for tt_create); larger problems return TT_INVALID_ARG.
+ * prob is validated like tt_create's; B_dev (device, [n_proj][n_seg][K]
+ * doubles, 16-byte aligned) receives the result, enqueued on stream
+ * (cudaStream_t, NULL = legacy default stream).  The first call on each
+ * device looks up the scratch array's device address (the device must be
+ * current); make that first call before any stream capture.  All calls
+ * share the one scratch array, which keeps the last call's contents; every
+ * call overwrites what it reads, so nothing needs clearing, but calls whose
+ * work overlaps on the GPU (other streams, other host threads) race on it. */
+tt_status tt_basis_matrix_noalloc(const tt_problem *prob, double *B_dev, void *stream);
+
 /* Forward model, Eq. (forward_model): I = A c.
  * c_dev [nx][ny][nz][K] -> I_dev [n_proj][nj][nk][n_seg]. */
 tt_status tt_project(tt_handle *h, const float *c_dev, float *I_dev);

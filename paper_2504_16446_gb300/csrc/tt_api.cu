@@ -182,7 +182,7 @@ template <>
 const std::vector<AdjParams<double>> &adj_params<double>(const tt_handle *h) { return h->adj_f64; }
 
 // Gauss-Legendre nodes/weights on [-1, 1] (Newton on the three-term recurrence).
-static void gauss_legendre(int n, double *x, double *w)
+void gauss_legendre(int n, double *x, double *w)
 {
     const double pi = 3.14159265358979323846;
     for (int i = 0; i < n; ++i) {
@@ -218,7 +218,7 @@ static bool finite_all(const double *a, int n)
     return true;
 }
 
-static tt_status validate(const tt_problem *P)
+tt_status validate(const tt_problem *P)
 {
     if (!P) return invalid("tt_create: null problem");
     if (P->nx < 1 || P->ny < 1 || P->nz < 1) return invalid("volume shape must be >= 1 in every axis");

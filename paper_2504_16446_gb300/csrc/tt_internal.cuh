@@ -116,6 +116,9 @@ namespace tt {
 
 void set_error(const std::string &msg);
 tt_status cuda_fail(cudaError_t e, const char *what);
+// Problem validation and Gauss-Legendre rule shared by the entry points.
+tt_status validate(const tt_problem *P);
+void gauss_legendre(int n, double *x, double *w);
 
 template <typename T>
 const std::vector<AdjParams<T>> &adj_params(const tt_handle *h);

@@ -68,6 +68,7 @@ SIGNATURES = {
     "tt_get_sizes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "tt_basis_matrix": (ctypes.c_int, [_P, _P]),
+    "tt_basis_matrix_noalloc": (ctypes.c_int, [ctypes.POINTER(_Problem), _P, _P]),
     "tt_project": (ctypes.c_int, [_P, _P, _P]),
     "tt_project_f64": (ctypes.c_int, [_P, _P, _P]),
     "tt_adjoint": (ctypes.c_int, [_P, _P, _P]),
