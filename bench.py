@@ -39,12 +39,12 @@ FLUSH_BYTES = 512 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-evals", type=float, default=2.0,
+    ap.add_argument("--cpu-sample-evals", type=float, default=4.0,
                     help="oracle sample size in full-workload gradient evaluations")
     return ap.parse_args()
 
@@ -84,7 +84,7 @@ def ncu_traffic(kernel: str):
 
 class Clocks:
     """nvidia-smi sampling during the timed region."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -92,6 +92,13 @@ class Clocks:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def __enter__(self):
         try:
@@ -99,7 +106,7 @@ class Clocks:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -117,11 +124,19 @@ class Clocks:
     def summary(self):
         if not self.proc or not self.path:
             return None
+        import datetime
         rows = []
         with open(self.path) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
                 if len(parts) >= 9:
+                    try:
+                        ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    except ValueError:
+                        continue
+                    # samples inside the timed region (a 0.25 s grace for the sampling period)
+                    if self.t0 is not None and not (self.t0 - 0.25 <= ts <= (self.t1 or ts) + 0.25):
+                        continue
                     rows.append(parts)
         os.unlink(self.path)
         if not rows:
@@ -210,6 +225,8 @@ def run_ours(args):
     losses = []
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
+        time.sleep(0.3)                 # let the sampler start
+        clk.mark_start()
         for _ in range(args.steps):
             flush.zero_()
             ev0.record()
@@ -219,6 +236,7 @@ def run_ours(args):
             times.append(ev0.elapsed_time(ev1))
             losses.append(loss)
         torch.cuda.synchronize()
+        clk.mark_end()
     launches = h.launch_count() - launches0
     prof = h.profile_read()
     h.profile(False)
@@ -299,7 +317,10 @@ def run_ours(args):
 
 
 def run_reference(args):
-    """The FP64 CPU oracle as it stands, on the host cores (rank 0 only)."""
+    """The FP64 CPU oracle as it stands, on the host cores (rank 0 only).
+    Each step evaluates the gradient over a subset of the projections, sized
+    so that the whole --warmup + --steps run takes about 90 s, and the rate is
+    scaled to the full workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -311,22 +332,23 @@ def run_reference(args):
     ph = synth.phantom(WORKLOAD)
     c_true = oracle.zonal_to_sh(st.ell_max, ph.dirs.reshape(-1, 3),
                                 ph.amps.reshape(-1, st.ell_max // 2 + 1)).reshape(st.volume_shape)
-    # data: the oracle's own projection of the phantom with Poisson noise
-    sub_fraction = 0.25     # each step: a quarter of the projections, scaled to the full workload
-    rates = []
-    step_times = []
-    I_full = None
+    g_all = oracle.Geometry(st.shape, st.nj, st.nk, st.ell_max, st.inner_angle, st.outer_angle,
+                            st.seg_start, st.seg_end)
+    I_full = synth.poisson_counts(oracle.forward(g_all, c_true), 1e4, seed=1)
+    W_full = np.ones_like(I_full)
+    c_eval = 0.5 * c_true
+    # size the per-step sample from a 2-projection probe
+    probe_rate, _, _ = cpu_oracle_rate(st, c_eval, I_full, W_full, 2.0 / st.S)
+    per_step_s = 90.0 / max(1, args.warmup + args.steps)
+    frac = min(1.0, max(1.0 / st.S, per_step_s * probe_rate))
+    step_times, evals = [], 0.0
+    sample = ""
     for it in range(args.warmup + args.steps):
-        if I_full is None:
-            g_all = oracle.Geometry(st.shape, st.nj, st.nk, st.ell_max, st.inner_angle, st.outer_angle,
-                                    st.seg_start, st.seg_end)
-            I_full = synth.poisson_counts(oracle.forward(g_all, c_true), 1e4, seed=1)
-        rate, dt, sample = cpu_oracle_rate(st, 0.5 * c_true, I_full, np.ones_like(I_full), sub_fraction)
+        rate, dt, sample = cpu_oracle_rate(st, c_eval, I_full, W_full, frac)
         if it >= args.warmup:
-            rates.append(rate)
             step_times.append(dt)
+            evals += rate * dt
     total = sum(step_times)
-    evals = len(step_times) * sub_fraction
     value = evals / total
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
