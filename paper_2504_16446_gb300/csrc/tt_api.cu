@@ -121,7 +121,7 @@ static ProjGeom make_geom(const tt_handle *h, int s)
     while (std::fabs(d[m]) < (1.0 - 1e-12) * mx) ++m;   // ties -> smallest axis
     const int u = (m == 0) ? 1 : 0;
     const int v = (m == 2) ? 1 : 2;
-    const int stride[3] = {h->N[1] * h->N[2], h->N[2], 1};
+    const int stride[3] = {(h->N[1] + 4) * (h->N[2] + 4), h->N[2] + 4, 1};   // padded volume
     const double ba = h->b / h->a;
     const double cj = 0.5 * (h->nj - 1) + h->joff[s], ck = 0.5 * (h->nk - 1) + h->koff[s];
     const double hm = 0.5 * (h->N[m] - 1), hu = 0.5 * (h->N[u] - 1), hv = 0.5 * (h->N[v] - 1);
@@ -279,8 +279,8 @@ template <typename T>
 static tt_status project_impl(tt_handle *h, const T *c, T *I)
 {
     if (bad_ptr(c) || bad_ptr(I)) return invalid("tt_project: device pointers must be non-null and 16-byte aligned");
-    TT_CUDA(launch_pack<T>(h, c, (T *)h->cpad), "pack");
-    TT_CUDA(launch_forward<T>(h, (const T *)h->cpad, I, nullptr, nullptr, false), "forward");
+    TT_CUDA(launch_pack<T>(h, c), "pack");
+    TT_CUDA(launch_forward<T>(h, I, nullptr, nullptr, false), "forward");
     return TT_OK;
 }
 
@@ -303,9 +303,9 @@ tt_status tt_grad_enqueue(tt_handle *h, const T *c, const T *I, const T *W, T *g
 {
     if (bad_ptr(c) || bad_ptr(I) || (W && bad_ptr(W)) || (g && bad_ptr(g)))
         return invalid("tt_gradient_residual: device pointers must be non-null (W, g may be NULL) and 16-byte aligned");
-    TT_CUDA(launch_pack<T>(h, c, (T *)h->cpad), "pack");
-    TT_CUDA(launch_forward<T>(h, (const T *)h->cpad, nullptr, I, W, true), "forward");
-    TT_CUDA(launch_reduce(h, h->partials, h->n_partials, h->loss_dev, nullptr, 1.0), "loss reduce");
+    TT_CUDA(launch_pack<T>(h, c), "pack");
+    TT_CUDA(launch_forward<T>(h, nullptr, I, W, true), "forward");
+    TT_CUDA(launch_reduce(h, h->partials, h->n_fwd_ctas, h->loss_dev, nullptr, 1.0), "loss reduce");
     if (g) TT_CUDA(launch_adjoint<T>(h, (const T *)h->G, g), "adjoint");
     return TT_OK;
 }
@@ -407,11 +407,17 @@ tt_status tt_create(const tt_problem *P, tt_precision prec, void *stream, tt_han
     ALLOC(h->geo, sizeof(ProjGeom) * h->S);
     ALLOC(h->B64, sizeof(double) * h->S * h->C * h->K);
     ALLOC(h->Bp, es * h->S * h->CP * h->KP);
-    ALLOC(h->cpad, es * h->nvox() * h->KP);
+    {
+        const long long padded = (long long)(h->N[0] + 4) * (h->N[1] + 4) * (h->N[2] + 4);
+        ALLOC(h->cpad, es * padded * h->KP);
+        h->cpad_origin = 2LL * (h->N[1] + 4) * (h->N[2] + 4) + 2LL * (h->N[2] + 4) + 2;
+        cudaError_t ez = cudaMemsetAsync(h->cpad, 0, es * padded * h->KP, h->stream);   // border stays zero
+        if (ez != cudaSuccess) { free_handle(h); return cuda_fail(ez, "tt_create: memset"); }
+    }
     ALLOC(h->gpad, es * h->nvox() * h->KP);
     ALLOC(h->G, es * h->npix() * h->KP);
-    h->n_partials = forward_ctas(h);
-    if (h->n_partials < kDotBlocks) h->n_partials = kDotBlocks;
+    h->n_fwd_ctas = forward_ctas(h);
+    h->n_partials = h->n_fwd_ctas;
     ALLOC(h->partials, sizeof(double) * h->n_partials);
     ALLOC(h->loss_dev, sizeof(double) * 4);
     {

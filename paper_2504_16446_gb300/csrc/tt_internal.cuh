@@ -44,7 +44,7 @@ struct ProjGeom {
     double hj, hk;
     int m, u, v;              // main and transverse axes (0=x, 1=y, 2=z)
     int Nm, Nu, Nv;
-    int sm, su, sv;           // voxel strides of the axes
+    int sm, su, sv;           // strides of the axes in the padded volume cpad
     int nwj, nwk;
 };
 
@@ -92,11 +92,13 @@ struct tt_handle {
     tt::ProjGeom *geo = nullptr;        // device [S]
     double *B64 = nullptr;               // device [S][C][K] FP64
     void *Bp = nullptr;                  // device [S][CP][KP], element type, zero padded
-    void *cpad = nullptr;                // device [nvox][KP]
+    void *cpad = nullptr;                // device [nx+4][ny+4][nz+4][KP], two-voxel zero border
+    long long cpad_origin = 0;           // voxel offset of (0,0,0) in cpad
     void *gpad = nullptr;                // device [nvox][KP]
     void *G = nullptr;                   // device [S][nj][nk][KP]
     double *partials = nullptr;          // device, per-CTA loss partials
-    long long n_partials = 0;
+    long long n_partials = 0;            // allocated entries
+    long long n_fwd_ctas = 0;            // entries the forward kernel writes
     double *loss_dev = nullptr;          // device scalar
     double *loss_pinned = nullptr;       // pinned host scalar
     // host-buffer entry point staging (allocated on first use)
@@ -132,12 +134,13 @@ void prof_begin(tt_handle *h, int slot, cudaEvent_t *ev);
 void prof_end(tt_handle *h, int slot, cudaEvent_t ev);
 
 // Kernel launchers (return the launch error, if any).
+// Packs c [nvox][K] into the interior of cpad (channels padded to KP).
 template <typename T>
-cudaError_t launch_pack(tt_handle *h, const T *c, T *cpad);
+cudaError_t launch_pack(tt_handle *h, const T *c);
 template <typename T>
 cudaError_t launch_unpack(tt_handle *h, const T *gpad, T *g);
 template <typename T>
-cudaError_t launch_forward(tt_handle *h, const T *cpad, T *Iout, const T *I, const T *W, bool grad);
+cudaError_t launch_forward(tt_handle *h, T *Iout, const T *I, const T *W, bool grad);
 template <typename T>
 cudaError_t launch_backcontract(tt_handle *h, const T *R, T *G);
 // g [nvox][K] (unpadded) = exact-transpose gather of G; S above one

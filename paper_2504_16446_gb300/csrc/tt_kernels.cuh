@@ -83,9 +83,10 @@ __device__ __forceinline__ double block_sum(double v, double *red)
     return t;
 }
 
-// Range of planes p in [0, Nm-1] on which coordinate w(p) = w0 + p*dw can
-// give a tap inside [0, N-1] (i.e. -1 < w < N), widened by one plane on each
-// side; per-tap bounds checks make the widening harmless.
+// Range of planes p in [0, Nm-1] on which coordinate w(p) = w0 + p*dw lies
+// in (-1, N), i.e. can give a bilinear tap inside [0, N-1].  floor/ceil of the
+// bounds may add one plane on each side; those planes see only the zero
+// border of the padded volume.
 template <typename T>
 __device__ __forceinline__ void clip_planes(T w0, T dw, int N, T &lo, T &hi)
 {
@@ -95,80 +96,23 @@ __device__ __forceinline__ void clip_planes(T w0, T dw, int N, T &lo, T &hi)
     }
     T inv = T(1) / dw;
     T p1 = (T(-1) - w0) * inv, p2 = (T(N) - w0) * inv;
-    lo = fmax(lo, fmin(p1, p2) - T(1));
-    hi = fmin(hi, fmax(p1, p2) + T(1));
+    lo = fmax(lo, fmin(p1, p2));
+    hi = fmin(hi, fmax(p1, p2));
 }
 
-// ------------------------------------------------------------ forward kernel
-//
-// One CTA = one projection s x one 8-wide tile of rays.  Each lane group
-// marches its ray along the main axis (Joseph's method, bilinear taps read
-// straight from the L1/L2-resident volume), scales by the step length, then
-//   PROJECT: writes I_hat = B_s Y                           (Eq. forward_model)
-//   GRAD:    r = I_hat - I, loss += W r^2, G = 2 B_s^T (W r) (Eq. residual)
-// The SH contraction runs four segments at a time: partial dot products over
-// the lane's channels, a butterfly across the lane group, then each lane
-// back-contracts into its own channels.
-template <typename T, int KP, int LG, bool GRAD>
-__global__ void __launch_bounds__(kThreads)
-k_forward(const ProjGeom *__restrict__ geo, const T *__restrict__ cpad, const T *__restrict__ Bp,
-          int nj, int nk, int C, int CP, int tiles_k,
-          T *__restrict__ Iout, const T *__restrict__ Id, const T *__restrict__ Wd,
-          T *__restrict__ G, double *__restrict__ partials)
+// SH contraction of a marched ray and, in GRAD mode, the residual, its
+// weighted square and the back-contraction (Eq. forward_model, Eq. residual).
+// The contraction runs four segments at a time: partial dot products over the
+// lane's CPL channels, a butterfly across the LG lanes of the channel group,
+// then each lane back-contracts into its own channels.  Lanes with
+// writer == false (duplicate halves) compute but do not store.  Returns the
+// ray's sum of W r^2 on every lane.
+template <typename T, int CPL, int KP, int LG, bool GRAD>
+__device__ __forceinline__ T forward_epilogue(const T (&acc)[CPL], int q, bool valid, bool writer, long long pix,
+                                              const T *__restrict__ Bs, int C, int CP, T *__restrict__ Iout,
+                                              const T *__restrict__ Id, const T *__restrict__ Wd,
+                                              T *__restrict__ G)
 {
-    constexpr int CPL = KP / LG;
-    constexpr int RAYS = kThreads / LG;
-    constexpr int TK = 8;
-    constexpr int TJ = RAYS / TK;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *Bs = reinterpret_cast<T *>(smem_raw);   // [CP][KP]
-    __shared__ double red[kThreads / 32];
-
-    const int s = blockIdx.y;
-    const int tj = blockIdx.x / tiles_k, tk = blockIdx.x % tiles_k;
-    const int r = threadIdx.x / LG, q = threadIdx.x % LG;
-    const int j = tj * TJ + r / TK, k = tk * TK + r % TK;
-    const bool valid = (j < nj) && (k < nk);
-
-    const T *Bsrc = Bp + (size_t)s * CP * KP;
-    for (int t = threadIdx.x; t < CP * KP; t += kThreads) Bs[t] = Bsrc[t];
-
-    const ProjGeom &P = geo[s];
-    // Ray base in FP64 (one rounding to T), per-plane stepping in T.
-    const double urd = P.u0 + (double)j * P.uj + (double)k * P.uk;
-    const double vrd = P.v0 + (double)j * P.vj + (double)k * P.vk;
-    const T ur = (T)urd, vr = (T)vrd, up = (T)P.up, vp = (T)P.vp;
-    const int Nu = P.Nu, Nv = P.Nv, sm = P.sm, su = P.su, sv = P.sv;
-    T lo = T(0), hi = T(P.Nm - 1);
-    clip_planes<T>(ur, up, Nu, lo, hi);
-    clip_planes<T>(vr, vp, Nv, lo, hi);
-    int plo = valid ? max(0, (int)floor(lo)) : 1;
-    int phi = valid ? min(P.Nm - 1, (int)ceil(hi)) : 0;
-
-    T acc[CPL];
-#pragma unroll
-    for (int i = 0; i < CPL; ++i) acc[i] = T(0);
-    const T *cq = cpad + q * CPL;
-    for (int p = plo; p <= phi; ++p) {
-        const T u = fma((T)p, up, ur), v = fma((T)p, vp, vr);
-        const T fu = floor(u), fv = floor(v);
-        const int iu = (int)fu, iv = (int)fv;
-        const T wu = u - fu, wv = v - fv;
-        const bool u0 = (unsigned)iu < (unsigned)Nu, u1 = (unsigned)(iu + 1) < (unsigned)Nu;
-        const bool v0 = (unsigned)iv < (unsigned)Nv, v1 = (unsigned)(iv + 1) < (unsigned)Nv;
-        const long long vox = (long long)p * sm + (long long)iu * su + (long long)iv * sv;
-        if (u0 && v0) fma_row<T, CPL>(acc, (T(1) - wu) * (T(1) - wv), cq + vox * KP);
-        if (u1 && v0) fma_row<T, CPL>(acc, wu * (T(1) - wv), cq + (vox + su) * KP);
-        if (u0 && v1) fma_row<T, CPL>(acc, (T(1) - wu) * wv, cq + (vox + sv) * KP);
-        if (u1 && v1) fma_row<T, CPL>(acc, wu * wv, cq + (vox + su + sv) * KP);
-    }
-    const T step = (T)P.step;
-#pragma unroll
-    for (int i = 0; i < CPL; ++i) acc[i] *= step;
-
-    __syncthreads();   // Bs staged
-
-    const long long pix = ((long long)s * nj + j) * nk + k;
     T gacc[CPL];
 #pragma unroll
     for (int i = 0; i < CPL; ++i) gacc[i] = T(0);
@@ -189,7 +133,7 @@ k_forward(const ProjGeom *__restrict__ geo, const T *__restrict__ cpad, const T 
 #pragma unroll
             for (int t = 0; t < 4; ++t) ih[t] += __shfl_xor_sync(0xffffffffu, ih[t], off);
         if constexpr (!GRAD) {
-            if (valid) {
+            if (valid && writer) {
 #pragma unroll
                 for (int t = 0; t < 4; ++t)
                     if ((t % LG) == q && c0 + t < C) Iout[pix * C + c0 + t] = ih[t];
@@ -238,7 +182,89 @@ k_forward(const ProjGeom *__restrict__ geo, const T *__restrict__ cpad, const T 
         }
     }
     if constexpr (GRAD) {
-        if (valid) store_row<T, CPL>(G + pix * KP + q * CPL, gacc, T(2));
+        if (valid && writer) store_row<T, CPL>(G + pix * KP + q * CPL, gacc, T(2));
+    }
+    return lossr;
+}
+
+// ------------------------------------------------------------ forward kernel
+//
+// One CTA = one projection s x one 8-wide tile of rays.  Each lane group
+// marches its ray along the main axis (Joseph's method, bilinear taps read
+// straight from the L1/L2-resident volume), scales by the step length, then
+//   PROJECT: writes I_hat = B_s Y                           (Eq. forward_model)
+//   GRAD:    r = I_hat - I, loss += W r^2, G = 2 B_s^T (W r) (Eq. residual)
+// The SH contraction runs four segments at a time: partial dot products over
+// the lane's channels, a butterfly across the lane group, then each lane
+// back-contracts into its own channels.
+template <typename T, int KP, int LG, bool GRAD>
+__global__ void __launch_bounds__(kThreads)
+k_forward(const ProjGeom *__restrict__ geo, const T *__restrict__ cpad /* interior origin */,
+          const T *__restrict__ Bp,
+          int nj, int nk, int C, int CP, int tiles_k,
+          T *__restrict__ Iout, const T *__restrict__ Id, const T *__restrict__ Wd,
+          T *__restrict__ G, double *__restrict__ partials)
+{
+    constexpr int CPL = KP / LG;
+    constexpr int RAYS = kThreads / LG;
+    constexpr int TK = 8;
+    constexpr int TJ = RAYS / TK;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Bs = reinterpret_cast<T *>(smem_raw);   // [CP][KP]
+    __shared__ double red[kThreads / 32];
+
+    const int s = blockIdx.y;
+    const int tj = blockIdx.x / tiles_k, tk = blockIdx.x % tiles_k;
+    const int r = threadIdx.x / LG, q = threadIdx.x % LG;
+    const int j = tj * TJ + r / TK, k = tk * TK + r % TK;
+    const bool valid = (j < nj) && (k < nk);
+
+    const T *Bsrc = Bp + (size_t)s * CP * KP;
+    for (int t = threadIdx.x; t < CP * KP; t += kThreads) Bs[t] = Bsrc[t];
+
+    const ProjGeom &P = geo[s];
+    // Ray base in FP64 (one rounding to T), per-plane stepping in T.
+    const double urd = P.u0 + (double)j * P.uj + (double)k * P.uk;
+    const double vrd = P.v0 + (double)j * P.vj + (double)k * P.vk;
+    const T ur = (T)urd, vr = (T)vrd, up = (T)P.up, vp = (T)P.vp;
+    const int Nu = P.Nu, Nv = P.Nv, sm = P.sm, su = P.su, sv = P.sv;
+    T lo = T(0), hi = T(P.Nm - 1);
+    clip_planes<T>(ur, up, Nu, lo, hi);
+    clip_planes<T>(vr, vp, Nv, lo, hi);
+    int plo = valid ? max(0, (int)floor(lo)) : 1;
+    int phi = valid ? min(P.Nm - 1, (int)ceil(hi)) : 0;
+
+    T acc[CPL];
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) acc[i] = T(0);
+    // cpad is the interior origin of a volume with a two-voxel zero border:
+    // every tap index in [-2, N+1] is a valid address, so the four loads need
+    // no bounds tests (indices are clamped to [-2, N] first, which only ever
+    // moves a tap pair that lies wholly in the border).
+    const T *cq = cpad + q * CPL;
+    const long long sub = (long long)su * KP, svb = (long long)sv * KP;
+#pragma unroll 1
+    for (int p = plo; p <= phi; ++p) {
+        const T u = fma((T)p, up, ur), v = fma((T)p, vp, vr);
+        const T fu = floor(u), fv = floor(v);
+        const int iu = min(max((int)fu, -2), Nu), iv = min(max((int)fv, -2), Nv);
+        const T wu = u - fu, wv = v - fv;
+        const T *t00 = cq + ((long long)p * sm + (long long)iu * su + (long long)iv * sv) * KP;
+        const T a0 = T(1) - wu, b0 = T(1) - wv;
+        fma_row<T, CPL>(acc, a0 * b0, t00);
+        fma_row<T, CPL>(acc, wu * b0, t00 + sub);
+        fma_row<T, CPL>(acc, a0 * wv, t00 + svb);
+        fma_row<T, CPL>(acc, wu * wv, t00 + sub + svb);
+    }
+    const T step = (T)P.step;
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) acc[i] *= step;
+
+    __syncthreads();   // Bs staged
+
+    const long long pix = ((long long)s * nj + j) * nk + k;
+    const T lossr = forward_epilogue<T, CPL, KP, LG, GRAD>(acc, q, valid, true, pix, Bs, C, CP, Iout, Id, Wd, G);
+    if constexpr (GRAD) {
         const double lv = (q == 0 && valid) ? (double)lossr : 0.0;
         const double tot = block_sum(lv, red);
         if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = tot;
@@ -297,6 +323,10 @@ template <typename T, int CPL, int KP, int LG, int NJ, int NK>
 __device__ __forceinline__ void adj_window(T (&acc)[LG][CPL], const T *__restrict__ Gq, int nk, int r0, T du0,
                                            T dv0, const AdjProj<T> &c, unsigned jmask, unsigned kmask)
 {
+    // window origin row of every source voxel of the group (one shuffle each)
+    int r0s[LG];
+#pragma unroll
+    for (int src = 0; src < LG; ++src) r0s[src] = (LG == 1) ? r0 : __shfl_sync(0xffffffffu, r0, src, LG);
 #pragma unroll
     for (int a = 0; a < NJ; ++a) {
 #pragma unroll
@@ -307,12 +337,11 @@ __device__ __forceinline__ void adj_window(T (&acc)[LG][CPL], const T *__restric
             const T tv = c.step - c.step * fabs(dv);
             const bool hit = ((jmask >> a) & (kmask >> b) & 1u) && tu > T(0) && tv > T(0);
             const T w = hit ? tu * tv : T(0);
-            const int row = r0 + a * nk + b;
+            const int off = a * nk + b;
 #pragma unroll
             for (int src = 0; src < LG; ++src) {
                 const T ws = (LG == 1) ? w : __shfl_sync(0xffffffffu, w, src, LG);
-                const int rs = (LG == 1) ? row : __shfl_sync(0xffffffffu, row, src, LG);
-                if (ws != T(0)) fma_row<T, CPL>(acc[src], ws, Gq + (long long)rs * KP);
+                if (ws != T(0)) fma_row<T, CPL>(acc[src], ws, Gq + (long long)(r0s[src] + off) * KP);
             }
         }
     }
@@ -343,7 +372,7 @@ __device__ __forceinline__ void adj_window_any(T (&acc)[LG][CPL], const T *__res
 }
 
 template <typename T, int KP, int LG>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, 3)
 k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const T *__restrict__ G, int nj, int nk, int nx,
           int ny, int nz, int ty, int tz, T *__restrict__ gpad, int accumulate, T *__restrict__ gout, int K)
 {
@@ -432,14 +461,14 @@ k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const T *__restrict__ 
 // ------------------------------------------------------------ launchers
 
 template <typename T, int L>
-cudaError_t launch_forward_L(tt_handle *h, const T *cpad, T *Iout, const T *I, const T *W, bool grad)
+cudaError_t launch_forward_L(tt_handle *h, T *Iout, const T *I, const T *W, bool grad)
 {
     constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K);
     constexpr int RAYS = kThreads / LG, TK = 8, TJ = RAYS / TK;
     const int tiles_k = (h->nk + TK - 1) / TK, tiles_j = (h->nj + TJ - 1) / TJ;
     dim3 grid(tiles_k * tiles_j, h->S);
     const size_t smem = (size_t)h->CP * KP * sizeof(T);
-    const T *Bp = (const T *)h->Bp;
+    const T *Bp = (const T *)h->Bp, *cpad = (const T *)h->cpad + h->cpad_origin * KP;
     cudaEvent_t ev;
     prof_begin(h, TT_KSLOT_FORWARD, &ev);
     if (grad) {

@@ -7,16 +7,19 @@ namespace tt {
 
 // ------------------------------------------------------------- layout
 
-// cpad[v][i] = c[v][i] for i < K, 0 for K <= i < KP.
+// Interior of the padded volume: cpad[x+2][y+2][z+2][i] = c[x][y][z][i] for
+// i < K, 0 for K <= i < KP (the two-voxel border is zeroed once at creation).
 template <typename T>
-__global__ void k_pack(const T *__restrict__ c, T *__restrict__ cpad, long long nvox, int K, int KP)
+__global__ void k_pack(const T *__restrict__ c, T *__restrict__ cpad, int nx, int ny, int nz, int K, int KP)
 {
-    const long long n = nvox * KP;
+    const long long n = (long long)nx * ny * nz * KP;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {
         const long long v = t / KP;
         const int i = (int)(t - v * KP);
-        cpad[t] = i < K ? __ldg(c + v * K + i) : T(0);
+        const int z = (int)(v % nz), y = (int)((v / nz) % ny), x = (int)(v / ((long long)nz * ny));
+        const long long o = (((long long)(x + 2) * (ny + 4) + (y + 2)) * (nz + 4) + (z + 2)) * KP + i;
+        cpad[o] = i < K ? __ldg(c + v * K + i) : T(0);
     }
 }
 
@@ -41,11 +44,12 @@ static unsigned grid_for(long long n, int per_block = 256)
 }
 
 template <typename T>
-cudaError_t launch_pack(tt_handle *h, const T *c, T *cpad)
+cudaError_t launch_pack(tt_handle *h, const T *c)
 {
     cudaEvent_t ev;
     prof_begin(h, TT_KSLOT_PACK, &ev);
-    k_pack<T><<<grid_for(h->nvox() * h->KP), 256, 0, h->stream>>>(c, cpad, h->nvox(), h->K, h->KP);
+    k_pack<T><<<grid_for(h->nvox() * h->KP), 256, 0, h->stream>>>(c, (T *)h->cpad, h->N[0], h->N[1], h->N[2], h->K,
+                                                                h->KP);
     cudaError_t e = cudaGetLastError();
     prof_end(h, TT_KSLOT_PACK, ev);
     return e;
@@ -62,8 +66,8 @@ cudaError_t launch_unpack(tt_handle *h, const T *gpad, T *g)
     return e;
 }
 
-template cudaError_t launch_pack<float>(tt_handle *, const float *, float *);
-template cudaError_t launch_pack<double>(tt_handle *, const double *, double *);
+template cudaError_t launch_pack<float>(tt_handle *, const float *);
+template cudaError_t launch_pack<double>(tt_handle *, const double *);
 template cudaError_t launch_unpack<float>(tt_handle *, const float *, float *);
 template cudaError_t launch_unpack<double>(tt_handle *, const double *, double *);
 

@@ -4,9 +4,9 @@
 namespace tt {
 
 template <>
-cudaError_t launch_forward<float>(tt_handle *h, const float *cpad, float *Iout, const float *I, const float *W, bool grad)
+cudaError_t launch_forward<float>(tt_handle *h, float *Iout, const float *I, const float *W, bool grad)
 {
-#define TT_CALL(L) launch_forward_L<float, L>(h, cpad, Iout, I, W, grad)
+#define TT_CALL(L) launch_forward_L<float, L>(h, Iout, I, W, grad)
     TT_DISPATCH_L(h->L, TT_CALL)
 #undef TT_CALL
 }

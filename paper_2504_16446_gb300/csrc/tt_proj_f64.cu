@@ -4,9 +4,9 @@
 namespace tt {
 
 template <>
-cudaError_t launch_forward<double>(tt_handle *h, const double *cpad, double *Iout, const double *I, const double *W, bool grad)
+cudaError_t launch_forward<double>(tt_handle *h, double *Iout, const double *I, const double *W, bool grad)
 {
-#define TT_CALL(L) launch_forward_L<double, L>(h, cpad, Iout, I, W, grad)
+#define TT_CALL(L) launch_forward_L<double, L>(h, Iout, I, W, grad)
     TT_DISPATCH_L(h->L, TT_CALL)
 #undef TT_CALL
 }
