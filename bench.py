@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-time-to-loss", action="store_true")
+    ap.add_argument("--ttl-ref-iters", type=int, default=300,
+                    help="L-BFGS iterations of the reference solve that defines L*")
     ap.add_argument("--cpu-sample-evals", type=float, default=4.0,
                     help="oracle sample size in full-workload gradient evaluations")
     return ap.parse_args()
@@ -193,6 +196,38 @@ def make_inputs(st, torch, tt, synth):
     return h, c, I, W
 
 
+def time_to_loss(h, I, W, torch, tt, ref_iters: int, target: float = 1e-3):
+    """Plain FP32 L-BFGS from zero: wall time, iterations and gradient
+    evaluations until the excess loss (L - L*) / (L0 - L*) <= target, where
+    L* is the loss after ref_iters iterations of the same solver."""
+    z = torch.zeros(h.volume_shape, dtype=torch.float32, device="cuda")
+    ref = tt.LBFGS(h, z, I, W, m=10)
+    L0 = ref.loss
+    for _ in range(ref_iters):
+        _, _, st = ref.step()
+        if st != tt.TT_OK:
+            break
+    Lstar = ref.loss
+    ref.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    opt = tt.LBFGS(h, z, I, W, m=10)
+    iters, evals = 0, 1
+    while (opt.loss - Lstar) > target * (L0 - Lstar) and iters < ref_iters:
+        _, ne, st = opt.step()
+        iters += 1
+        evals += ne
+        if st != tt.TT_OK:
+            break
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    reached = (opt.loss - Lstar) <= target * (L0 - Lstar)
+    opt.close()
+    return {"seconds": dt, "iterations": iters, "evals": evals, "reached": bool(reached),
+            "criterion": f"(L - L*)/(L0 - L*) <= {target:g}, L* = loss after {ref_iters} L-BFGS iterations (m=10)",
+            "L0": L0, "L_star": Lstar}
+
+
 def run_ours(args):
     import torch
     from paper_2504_16446_gb300 import build, synth, tt
@@ -305,6 +340,8 @@ def run_ours(args):
         "clocks": clocks,
         "loss": losses[-1],
     }
+    if not args.no_time_to_loss:
+        out["time_to_loss"] = {"plain_f32": time_to_loss(h, I, W, torch, tt, args.ttl_ref_iters)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, dt, sample = cpu_oracle_rate(st, c.cpu().numpy(), I.cpu().numpy(), W.cpu().numpy(),
                                            args.cpu_sample_evals)
