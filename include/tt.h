@@ -161,6 +161,21 @@ tt_status tt_gradient_residual_f64(tt_handle *h, const double *c_dev, const doub
 tt_status tt_gradient_residual_host(tt_handle *h, const float *c_host, const float *I_host,
                                     const float *W_host, float *g_host, double *loss_host);
 
+/* Regularisers (Section "Optimization": L2Norm, TotalVariation) of a volume
+ * c_dev [nx][ny][nz][K] of the handle's shape; FP64 accumulation of the
+ * value; grad_dev (may be NULL) receives the gradient; value_host is a HOST
+ * pointer and the call synchronises the handle's stream.
+ *   tt_l2_norm:  value = sum c^2, grad = 2 c.
+ *   tt_tv_huber: value = sum over voxels x and channels i of H(|g_i(x)|),
+ *     g_i(x)_d = c_i(x + e_d) - c_i(x) for x_d + 1 < N_d else 0 (forward
+ *     differences, Neumann boundary), |.| Euclidean over d = x, y, z, and
+ *     H(t) = t^2 / (2 delta) for t <= delta, t - delta/2 otherwise (delta > 0).
+ * Returns TT_NONFINITE when the value is not finite. */
+tt_status tt_l2_norm(tt_handle *h, const float *c_dev, float *grad_dev, double *value_host);
+tt_status tt_l2_norm_f64(tt_handle *h, const double *c_dev, double *grad_dev, double *value_host);
+tt_status tt_tv_huber(tt_handle *h, const float *c_dev, double delta, float *grad_dev, double *value_host);
+tt_status tt_tv_huber_f64(tt_handle *h, const double *c_dev, double delta, double *grad_dev, double *value_host);
+
 /* L-BFGS (Section "Optimization"), unbounded two-loop recursion with memory
  * m and backtracking Armijo line search (c1 = 1e-4, step halving, at most 20
  * evaluations per iteration; first iteration steps 1/|g| along -g; a pair is

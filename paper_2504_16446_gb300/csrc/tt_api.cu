@@ -258,7 +258,7 @@ static void free_handle(tt_handle *h)
 {
     if (!h) return;
     cudaFree(h->geo); cudaFree(h->B64); cudaFree(h->Bp); cudaFree(h->cpad); cudaFree(h->gpad);
-    cudaFree(h->G); cudaFree(h->partials); cudaFree(h->loss_dev);
+    cudaFree(h->G); cudaFree(h->partials); cudaFree(h->loss_dev); cudaFree(h->red);
     cudaFree(h->hc); cudaFree(h->hI); cudaFree(h->hW); cudaFree(h->hg);
     if (h->loss_pinned) cudaFreeHost(h->loss_pinned);
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
@@ -420,6 +420,7 @@ tt_status tt_create(const tt_problem *P, tt_precision prec, void *stream, tt_han
     h->n_partials = h->n_fwd_ctas;
     ALLOC(h->partials, sizeof(double) * h->n_partials);
     ALLOC(h->loss_dev, sizeof(double) * 4);
+    ALLOC(h->red, sizeof(double) * kDotBlocks);
     {
         cudaError_t e = cudaMallocHost((void **)&h->loss_pinned, sizeof(double) * 4);
         if (e != cudaSuccess) { free_handle(h); return cuda_fail(e, "tt_create: cudaMallocHost"); }

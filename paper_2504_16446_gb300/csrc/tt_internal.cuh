@@ -99,7 +99,8 @@ struct tt_handle {
     double *partials = nullptr;          // device, per-CTA loss partials
     long long n_partials = 0;            // allocated entries
     long long n_fwd_ctas = 0;            // entries the forward kernel writes
-    double *loss_dev = nullptr;          // device scalar
+    double *red = nullptr;               // device, kDotBlocks partials of the regulariser reductions
+    double *loss_dev = nullptr;          // device scalars: [0] loss, [1] regulariser value
     double *loss_pinned = nullptr;       // pinned host scalar
     // host-buffer entry point staging (allocated on first use)
     void *hc = nullptr, *hI = nullptr, *hW = nullptr, *hg = nullptr;

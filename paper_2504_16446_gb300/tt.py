@@ -76,6 +76,10 @@ SIGNATURES = {
     "tt_gradient_residual": (ctypes.c_int, [_P, _P, _P, _P, _P, _D]),
     "tt_gradient_residual_f64": (ctypes.c_int, [_P, _P, _P, _P, _P, _D]),
     "tt_gradient_residual_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _D]),
+    "tt_l2_norm": (ctypes.c_int, [_P, _P, _P, _D]),
+    "tt_l2_norm_f64": (ctypes.c_int, [_P, _P, _P, _D]),
+    "tt_tv_huber": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _D]),
+    "tt_tv_huber_f64": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _D]),
     "tt_lbfgs_create": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(_P)]),
     "tt_lbfgs_step": (ctypes.c_int, [_P, _P, _P, _D, ctypes.POINTER(ctypes.c_int)]),
     "tt_lbfgs_get": (ctypes.c_int, [_P, _P, _P, _P, _D]),
@@ -248,6 +252,26 @@ class Handle:
             None if W is None else W.ctypes.data_as(_P), g.ctypes.data_as(_P), ctypes.byref(loss)),
             "tt_gradient_residual_host")
         return loss.value, g
+
+    def l2_norm(self, c, want_grad=True):
+        """(sum c^2, 2c)."""
+        self._sync_stream()
+        g = torch.empty(self.volume_shape, dtype=self.dtype, device=c.device) if want_grad else None
+        v = ctypes.c_double(0.0)
+        fn = getattr(self.lib, "tt_l2_norm" + self._sfx)
+        _check(fn(self._h, _dptr(c, self.dtype, self.volume_shape, "c"),
+                  None if g is None else ctypes.c_void_p(g.data_ptr()), ctypes.byref(v)), "tt_l2_norm")
+        return v.value, g
+
+    def tv_huber(self, c, delta, want_grad=True):
+        """(Huber total variation, gradient); see tt_tv_huber in include/tt.h."""
+        self._sync_stream()
+        g = torch.empty(self.volume_shape, dtype=self.dtype, device=c.device) if want_grad else None
+        v = ctypes.c_double(0.0)
+        fn = getattr(self.lib, "tt_tv_huber" + self._sfx)
+        _check(fn(self._h, _dptr(c, self.dtype, self.volume_shape, "c"), float(delta),
+                  None if g is None else ctypes.c_void_p(g.data_ptr()), ctypes.byref(v)), "tt_tv_huber")
+        return v.value, g
 
     # ------------------------------------------------------------ profiling
     def profile(self, enable: bool = True):
