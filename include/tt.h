@@ -29,9 +29,9 @@
  *       basis    B[n_proj][n_seg][K]   (FP64)
  *     Every device pointer must be 16-byte aligned (any cudaMalloc / torch
  *     allocation is).  Internal padding of K is invisible to the caller.
- *   - Element type: float for a TT_F32 handle, double for a TT_F64 handle
- *     (entry points with the _f64 suffix).  Calling the other kind returns
- *     TT_INVALID_ARG.
+ *   - Element type: float for a TT_F32, TT_BF16 or TT_F16 handle, double for a
+ *     TT_F64 handle (entry points with the _f64 suffix).  Calling the other
+ *     kind returns TT_INVALID_ARG.
  *   - All work is enqueued on the handle's stream, in stream order.  Only
  *     entry points that return a host value (loss) synchronise that stream.
  *   - Inputs are never modified, except arguments named *_inout.
@@ -56,7 +56,15 @@ typedef enum {
     TT_CUDA_ERROR = 6         /* a CUDA runtime call or kernel launch failed */
 } tt_status;
 
-typedef enum { TT_F32 = 0, TT_F64 = 1 } tt_precision;
+/* Precision of a handle.  TT_F32 and TT_F64: storage and arithmetic in that
+ * type.  TT_BF16 and TT_F16 (the reduced-precision form): the entry points
+ * take and return float like TT_F32, but the coefficient volume and the
+ * back-contracted residual are stored inside the path as bfloat16 / float16
+ * (halving their traffic), with float arithmetic, Kahan-compensated ray
+ * sums, and FP64 loss and dot-product reductions.  Their results differ from
+ * FP32 by the 2-byte rounding of those two intermediates (relative ~1e-3 for
+ * bfloat16, ~1e-4 for float16). */
+typedef enum { TT_F32 = 0, TT_F64 = 1, TT_BF16 = 2, TT_F16 = 3 } tt_precision;
 
 /* Unit vectors of the instrument in laboratory coordinates, Table
  * "geometry_vectors": beam p, raster directions j and k, detector azimuth
@@ -194,6 +202,7 @@ tt_status tt_lbfgs_step(tt_handle *h, tt_lbfgs *st, void *c_out_dev, double *los
                         int *n_evals_host);
 /* Current iterate / gradient / loss of the state. */
 tt_status tt_lbfgs_get(tt_handle *h, tt_lbfgs *st, void *c_dev, void *g_dev, double *loss_host);
+/* Frees the state; valid before or after tt_destroy of its handle. */
 tt_status tt_lbfgs_destroy(tt_lbfgs *st);
 
 /* Phantom helper: SH coefficients of zonal functions rotated to unit axes n,

@@ -4,6 +4,10 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "tt_internal.cuh"
 
@@ -275,22 +279,40 @@ static long long forward_ctas(const tt_handle *h)
 // Checks a device pointer argument: non-null, 16-byte aligned.
 static bool bad_ptr(const void *p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
 
+// Calls f.template operator()<S>() with the storage type S of the handle's
+// coefficient volume and G (T itself, or bf16 / f16 for a float handle).
+template <typename T, typename F>
+static tt_status with_storage(const tt_handle *h, F &&f)
+{
+    if constexpr (std::is_same<T, double>::value) {
+        return f.template operator()<double>();
+    } else {
+        if (h->prec == TT_BF16) return f.template operator()<__nv_bfloat16>();
+        if (h->prec == TT_F16) return f.template operator()<__half>();
+        return f.template operator()<float>();
+    }
+}
+
 template <typename T>
 static tt_status project_impl(tt_handle *h, const T *c, T *I)
 {
     if (bad_ptr(c) || bad_ptr(I)) return invalid("tt_project: device pointers must be non-null and 16-byte aligned");
-    TT_CUDA(launch_pack<T>(h, c), "pack");
-    TT_CUDA(launch_forward<T>(h, I, nullptr, nullptr, false), "forward");
-    return TT_OK;
+    return with_storage<T>(h, [&]<typename S>() -> tt_status {
+        TT_CUDA((launch_pack<T, S>(h, c)), "pack");
+        TT_CUDA((launch_forward<T, S>(h, I, nullptr, nullptr, false)), "forward");
+        return TT_OK;
+    });
 }
 
 template <typename T>
 static tt_status adjoint_impl(tt_handle *h, const T *R, T *g)
 {
     if (bad_ptr(R) || bad_ptr(g)) return invalid("tt_adjoint: device pointers must be non-null and 16-byte aligned");
-    TT_CUDA(launch_backcontract<T>(h, R, (T *)h->G), "backcontract");
-    TT_CUDA(launch_adjoint<T>(h, (const T *)h->G, g), "adjoint");
-    return TT_OK;
+    return with_storage<T>(h, [&]<typename S>() -> tt_status {
+        TT_CUDA((launch_backcontract<T, S>(h, R)), "backcontract");
+        TT_CUDA((launch_adjoint<T, S>(h, g)), "adjoint");
+        return TT_OK;
+    });
 }
 
 }  // namespace tt
@@ -303,11 +325,13 @@ tt_status tt_grad_enqueue(tt_handle *h, const T *c, const T *I, const T *W, T *g
 {
     if (bad_ptr(c) || bad_ptr(I) || (W && bad_ptr(W)) || (g && bad_ptr(g)))
         return invalid("tt_gradient_residual: device pointers must be non-null (W, g may be NULL) and 16-byte aligned");
-    TT_CUDA(launch_pack<T>(h, c), "pack");
-    TT_CUDA(launch_forward<T>(h, nullptr, I, W, true), "forward");
-    TT_CUDA(launch_reduce(h, h->partials, h->n_fwd_ctas, h->loss_dev, nullptr, 1.0), "loss reduce");
-    if (g) TT_CUDA(launch_adjoint<T>(h, (const T *)h->G, g), "adjoint");
-    return TT_OK;
+    return with_storage<T>(h, [&]<typename S>() -> tt_status {
+        TT_CUDA((launch_pack<T, S>(h, c)), "pack");
+        TT_CUDA((launch_forward<T, S>(h, nullptr, I, W, true)), "forward");
+        TT_CUDA(launch_reduce(h, h->partials, h->n_fwd_ctas, h->loss_dev, nullptr, 1.0), "loss reduce");
+        if (g) TT_CUDA((launch_adjoint<T, S>(h, g)), "adjoint");
+        return TT_OK;
+    });
 }
 template tt_status tt_grad_enqueue<float>(tt_handle *, const float *, const float *, const float *, float *);
 template tt_status tt_grad_enqueue<double>(tt_handle *, const double *, const double *, const double *, double *);
@@ -334,10 +358,13 @@ static tt_status grad_impl(tt_handle *h, const T *c, const T *I, const T *W, T *
     return tt_read_loss(h, loss_host);
 }
 
+// want = TT_F32 for the float entry points (handles of precision TT_F32,
+// TT_BF16 or TT_F16), TT_F64 for the _f64 ones.
 static tt_status check_handle(const tt_handle *h, tt_precision want)
 {
     if (!h) return invalid("null handle");
-    if (h->prec != want) return invalid("handle precision does not match the entry point (use the _f64 variants with TT_F64)");
+    if ((h->prec == TT_F64) != (want == TT_F64))
+        return invalid("handle precision does not match the entry point (use the _f64 variants with TT_F64)");
     return TT_OK;
 }
 
@@ -367,7 +394,8 @@ tt_status tt_create(const tt_problem *P, tt_precision prec, void *stream, tt_han
     *out = nullptr;
     tt_status st = validate(P);
     if (st != TT_OK) return st;
-    if (prec != TT_F32 && prec != TT_F64) return invalid("precision must be TT_F32 or TT_F64");
+    if (prec != TT_F32 && prec != TT_F64 && prec != TT_BF16 && prec != TT_F16)
+        return invalid("precision must be TT_F32, TT_F64, TT_BF16 or TT_F16");
     if (P->ell_max > kMaxEll) {
         set_error("ell_max above 12 has no compiled kernels");
         return TT_UNSUPPORTED;
@@ -395,7 +423,7 @@ tt_status tt_create(const tt_problem *P, tt_precision prec, void *stream, tt_han
     h->seg1.assign(P->seg_end, P->seg_end + h->C);
     h->geo_host.resize(h->S);
     for (int s = 0; s < h->S; ++s) h->geo_host[s] = make_geom(h, s);
-    if (prec == TT_F32) build_adj_params<float>(h, h->adj_f32);
+    if (prec != TT_F64) build_adj_params<float>(h, h->adj_f32);
     else build_adj_params<double>(h, h->adj_f64);
 
     const size_t es = h->esize();
@@ -409,13 +437,13 @@ tt_status tt_create(const tt_problem *P, tt_precision prec, void *stream, tt_han
     ALLOC(h->Bp, es * h->S * h->CP * h->KP);
     {
         const long long padded = (long long)(h->N[0] + 4) * (h->N[1] + 4) * (h->N[2] + 4);
-        ALLOC(h->cpad, es * padded * h->KP);
+        ALLOC(h->cpad, h->ssize() * padded * h->KP);
         h->cpad_origin = 2LL * (h->N[1] + 4) * (h->N[2] + 4) + 2LL * (h->N[2] + 4) + 2;
-        cudaError_t ez = cudaMemsetAsync(h->cpad, 0, es * padded * h->KP, h->stream);   // border stays zero
+        cudaError_t ez = cudaMemsetAsync(h->cpad, 0, h->ssize() * padded * h->KP, h->stream);   // border stays zero
         if (ez != cudaSuccess) { free_handle(h); return cuda_fail(ez, "tt_create: memset"); }
     }
     ALLOC(h->gpad, es * h->nvox() * h->KP);
-    ALLOC(h->G, es * h->npix() * h->KP);
+    ALLOC(h->G, h->ssize() * h->npix() * h->KP);
     h->n_fwd_ctas = forward_ctas(h);
     h->n_partials = h->n_fwd_ctas;
     ALLOC(h->partials, sizeof(double) * h->n_partials);
@@ -442,7 +470,7 @@ tt_status tt_create(const tt_problem *P, tt_precision prec, void *stream, tt_han
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->geo, h->geo_host.data(), sizeof(ProjGeom) * h->S, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = launch_basis(h, dstage, dstage + kQuadNodes);
-    if (e == cudaSuccess) e = (prec == TT_F32) ? launch_cast_basis<float>(h) : launch_cast_basis<double>(h);
+    if (e == cudaSuccess) e = (prec != TT_F64) ? launch_cast_basis<float>(h) : launch_cast_basis<double>(h);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(dstage);
     if (e != cudaSuccess) {

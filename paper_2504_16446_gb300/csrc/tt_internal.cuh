@@ -112,7 +112,8 @@ struct tt_handle {
     long long nvox() const { return (long long)N[0] * N[1] * N[2]; }
     long long npix() const { return (long long)S * nj * nk; }
     long long ndata() const { return npix() * C; }
-    size_t esize() const { return prec == TT_F64 ? 8 : 4; }
+    size_t esize() const { return prec == TT_F64 ? 8 : 4; }                 // API element
+    size_t ssize() const { return prec == TT_BF16 || prec == TT_F16 ? 2 : esize(); }  // cpad, G storage
 };
 
 namespace tt {
@@ -136,18 +137,20 @@ void prof_end(tt_handle *h, int slot, cudaEvent_t ev);
 
 // Kernel launchers (return the launch error, if any).
 // Packs c [nvox][K] into the interior of cpad (channels padded to KP).
-template <typename T>
+template <typename T, typename S>
 cudaError_t launch_pack(tt_handle *h, const T *c);
 template <typename T>
 cudaError_t launch_unpack(tt_handle *h, const T *gpad, T *g);
-template <typename T>
+// Projector launchers: arithmetic in T, the coefficient volume cpad and the
+// back-contracted residual G stored as S (S = T, or a 2-byte type for T = float).
+template <typename T, typename S>
 cudaError_t launch_forward(tt_handle *h, T *Iout, const T *I, const T *W, bool grad);
-template <typename T>
-cudaError_t launch_backcontract(tt_handle *h, const T *R, T *G);
+template <typename T, typename S>
+cudaError_t launch_backcontract(tt_handle *h, const T *R);
 // g [nvox][K] (unpadded) = exact-transpose gather of G; S above one
 // parameter block runs several launches accumulating in h->gpad.
-template <typename T>
-cudaError_t launch_adjoint(tt_handle *h, const T *G, T *g);
+template <typename T, typename S>
+cudaError_t launch_adjoint(tt_handle *h, T *g);
 cudaError_t launch_reduce(tt_handle *h, const double *partials, long long n, double *out,
                           const double *add, double mul);
 cudaError_t launch_basis(tt_handle *h, const double *nodes, const double *weights);
@@ -158,7 +161,7 @@ cudaError_t launch_cast_basis(tt_handle *h);
 template <typename T>
 cudaError_t vec_dot(tt_handle *h, const T *x, const T *y, long long n, double *partials,
                     double *out, const double *add, double mul);
-// y = a*x + b*y with a = ha * (da ? *da : 1), b = hb
+// y = a*x + b*y with a = ha * (da ? *da : 1), b = hb (y is not read when hb == 0)
 template <typename T>
 cudaError_t vec_axpby(tt_handle *h, T *y, const T *x, long long n, double ha, const double *da, double hb);
 template <typename T>

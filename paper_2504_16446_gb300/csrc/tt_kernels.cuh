@@ -12,7 +12,11 @@
 // vector loads.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "tt_internal.cuh"
@@ -57,6 +61,76 @@ __device__ __forceinline__ void store_row(T *__restrict__ p, const T (&v)[CPL], 
 #pragma unroll
         for (int t = 0; t < CPL / 2; ++t)
             reinterpret_cast<double2 *>(p)[t] = make_double2(scale * v[2 * t], scale * v[2 * t + 1]);
+    }
+}
+
+// ------------------------------------------------ reduced-precision storage
+// The coefficient volume and the back-contracted residual G may be stored as
+// S = __nv_bfloat16 or __half while all arithmetic stays in T = float.  These
+// helpers read / write CPL consecutive elements of a row in S.
+__device__ __forceinline__ float2 unpack2(unsigned u, __nv_bfloat16 *)
+{
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u));
+}
+__device__ __forceinline__ float2 unpack2(unsigned u, __half *)
+{
+    return __half22float2(*reinterpret_cast<const __half2 *>(&u));
+}
+__device__ __forceinline__ unsigned pack2(float a, float b, __nv_bfloat16 *)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<unsigned *>(&v);
+}
+__device__ __forceinline__ unsigned pack2(float a, float b, __half *)
+{
+    __half2 v = __floats2half2_rn(a, b);
+    return *reinterpret_cast<unsigned *>(&v);
+}
+
+template <typename T, typename S, int CPL>
+__device__ __forceinline__ void fma_row_s(T (&acc)[CPL], T w, const S *__restrict__ p)
+{
+    if constexpr (std::is_same<T, S>::value) {
+        fma_row<T, CPL>(acc, w, p);
+    } else {
+        static_assert(sizeof(S) == 2 && CPL % 4 == 0, "2-byte storage rows are read 4 or 8 elements at a time");
+        if constexpr (CPL % 8 == 0) {
+#pragma unroll
+            for (int t = 0; t < CPL / 8; ++t) {
+                const uint4 u = __ldg(reinterpret_cast<const uint4 *>(p) + t);
+                const unsigned uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 f = unpack2(uu[k], (S *)nullptr);
+                    acc[8 * t + 2 * k] = fmaf(w, f.x, acc[8 * t + 2 * k]);
+                    acc[8 * t + 2 * k + 1] = fmaf(w, f.y, acc[8 * t + 2 * k + 1]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < CPL / 4; ++t) {
+                const uint2 u = __ldg(reinterpret_cast<const uint2 *>(p) + t);
+                const float2 f0 = unpack2(u.x, (S *)nullptr), f1 = unpack2(u.y, (S *)nullptr);
+                acc[4 * t] = fmaf(w, f0.x, acc[4 * t]);
+                acc[4 * t + 1] = fmaf(w, f0.y, acc[4 * t + 1]);
+                acc[4 * t + 2] = fmaf(w, f1.x, acc[4 * t + 2]);
+                acc[4 * t + 3] = fmaf(w, f1.y, acc[4 * t + 3]);
+            }
+        }
+    }
+}
+
+template <typename T, typename S, int CPL>
+__device__ __forceinline__ void store_row_s(S *__restrict__ p, const T (&v)[CPL], T scale)
+{
+    if constexpr (std::is_same<T, S>::value) {
+        store_row<T, CPL>(p, v, scale);
+    } else {
+#pragma unroll
+        for (int t = 0; t < CPL / 4; ++t)
+            reinterpret_cast<uint2 *>(p)[t] =
+                make_uint2(pack2(scale * v[4 * t], scale * v[4 * t + 1], (S *)nullptr),
+                           pack2(scale * v[4 * t + 2], scale * v[4 * t + 3], (S *)nullptr));
     }
 }
 
@@ -107,11 +181,11 @@ __device__ __forceinline__ void clip_planes(T w0, T dw, int N, T &lo, T &hi)
 // then each lane back-contracts into its own channels.  Lanes with
 // writer == false (duplicate halves) compute but do not store.  Returns the
 // ray's sum of W r^2 on every lane.
-template <typename T, int CPL, int KP, int LG, bool GRAD>
+template <typename T, typename S, int CPL, int KP, int LG, bool GRAD>
 __device__ __forceinline__ T forward_epilogue(const T (&acc)[CPL], int q, bool valid, bool writer, long long pix,
                                               const T *__restrict__ Bs, int C, int CP, T *__restrict__ Iout,
                                               const T *__restrict__ Id, const T *__restrict__ Wd,
-                                              T *__restrict__ G)
+                                              S *__restrict__ G)
 {
     T gacc[CPL];
 #pragma unroll
@@ -182,7 +256,7 @@ __device__ __forceinline__ T forward_epilogue(const T (&acc)[CPL], int q, bool v
         }
     }
     if constexpr (GRAD) {
-        if (valid && writer) store_row<T, CPL>(G + pix * KP + q * CPL, gacc, T(2));
+        if (valid && writer) store_row_s<T, S, CPL>(G + pix * KP + q * CPL, gacc, T(2));
     }
     return lossr;
 }
@@ -197,13 +271,13 @@ __device__ __forceinline__ T forward_epilogue(const T (&acc)[CPL], int q, bool v
 // The SH contraction runs four segments at a time: partial dot products over
 // the lane's channels, a butterfly across the lane group, then each lane
 // back-contracts into its own channels.
-template <typename T, int KP, int LG, bool GRAD>
+template <typename T, typename S, int KP, int LG, bool GRAD>
 __global__ void __launch_bounds__(kThreads)
-k_forward(const ProjGeom *__restrict__ geo, const T *__restrict__ cpad /* interior origin */,
+k_forward(const ProjGeom *__restrict__ geo, const S *__restrict__ cpad /* interior origin */,
           const T *__restrict__ Bp,
           int nj, int nk, int C, int CP, int tiles_k,
           T *__restrict__ Iout, const T *__restrict__ Id, const T *__restrict__ Wd,
-          T *__restrict__ G, double *__restrict__ partials)
+          S *__restrict__ G, double *__restrict__ partials)
 {
     constexpr int CPL = KP / LG;
     constexpr int RAYS = kThreads / LG;
@@ -241,20 +315,43 @@ k_forward(const ProjGeom *__restrict__ geo, const T *__restrict__ cpad /* interi
     // every tap index in [-2, N+1] is a valid address, so the four loads need
     // no bounds tests (indices are clamped to [-2, N] first, which only ever
     // moves a tap pair that lies wholly in the border).
-    const T *cq = cpad + q * CPL;
+    const S *cq = cpad + q * CPL;
     const long long sub = (long long)su * KP, svb = (long long)sv * KP;
+    // Reduced-precision storage: each plane's bilinear sum is formed in T and
+    // added to the ray sum with Kahan compensation.
+    constexpr bool COMP = !std::is_same<T, S>::value;
+    T comp[COMP ? CPL : 1];
+#pragma unroll
+    for (int i = 0; i < (COMP ? CPL : 1); ++i) comp[i] = T(0);
 #pragma unroll 1
     for (int p = plo; p <= phi; ++p) {
         const T u = fma((T)p, up, ur), v = fma((T)p, vp, vr);
         const T fu = floor(u), fv = floor(v);
         const int iu = min(max((int)fu, -2), Nu), iv = min(max((int)fv, -2), Nv);
         const T wu = u - fu, wv = v - fv;
-        const T *t00 = cq + ((long long)p * sm + (long long)iu * su + (long long)iv * sv) * KP;
+        const S *t00 = cq + ((long long)p * sm + (long long)iu * su + (long long)iv * sv) * KP;
         const T a0 = T(1) - wu, b0 = T(1) - wv;
-        fma_row<T, CPL>(acc, a0 * b0, t00);
-        fma_row<T, CPL>(acc, wu * b0, t00 + sub);
-        fma_row<T, CPL>(acc, a0 * wv, t00 + svb);
-        fma_row<T, CPL>(acc, wu * wv, t00 + sub + svb);
+        if constexpr (!COMP) {
+            fma_row_s<T, S, CPL>(acc, a0 * b0, t00);
+            fma_row_s<T, S, CPL>(acc, wu * b0, t00 + sub);
+            fma_row_s<T, S, CPL>(acc, a0 * wv, t00 + svb);
+            fma_row_s<T, S, CPL>(acc, wu * wv, t00 + sub + svb);
+        } else {
+            T pl[CPL];
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) pl[i] = T(0);
+            fma_row_s<T, S, CPL>(pl, a0 * b0, t00);
+            fma_row_s<T, S, CPL>(pl, wu * b0, t00 + sub);
+            fma_row_s<T, S, CPL>(pl, a0 * wv, t00 + svb);
+            fma_row_s<T, S, CPL>(pl, wu * wv, t00 + sub + svb);
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                const T y = pl[i] - comp[i];
+                const T t = acc[i] + y;
+                comp[i] = (t - acc[i]) - y;
+                acc[i] = t;
+            }
+        }
     }
     const T step = (T)P.step;
 #pragma unroll
@@ -263,7 +360,7 @@ k_forward(const ProjGeom *__restrict__ geo, const T *__restrict__ cpad /* interi
     __syncthreads();   // Bs staged
 
     const long long pix = ((long long)s * nj + j) * nk + k;
-    const T lossr = forward_epilogue<T, CPL, KP, LG, GRAD>(acc, q, valid, true, pix, Bs, C, CP, Iout, Id, Wd, G);
+    const T lossr = forward_epilogue<T, S, CPL, KP, LG, GRAD>(acc, q, valid, true, pix, Bs, C, CP, Iout, Id, Wd, G);
     if constexpr (GRAD) {
         const double lv = (q == 0 && valid) ? (double)lossr : 0.0;
         const double tot = block_sum(lv, red);
@@ -273,9 +370,9 @@ k_forward(const ProjGeom *__restrict__ geo, const T *__restrict__ cpad /* interi
 
 // ----------------------------------------------------- back-contraction
 // G[pix][i] = sum_c B[s][c][i] R[pix][c]  (the SH part of A^T).
-template <typename T, int KP, int LG>
+template <typename T, typename S, int KP, int LG>
 __global__ void __launch_bounds__(kThreads)
-k_backcontract(const T *__restrict__ Bp, const T *__restrict__ R, T *__restrict__ G,
+k_backcontract(const T *__restrict__ Bp, const T *__restrict__ R, S *__restrict__ G,
                long long npix, int njk, int C, int CP)
 {
     constexpr int CPL = KP / LG;
@@ -293,7 +390,7 @@ k_backcontract(const T *__restrict__ Bp, const T *__restrict__ R, T *__restrict_
 #pragma unroll
         for (int i = 0; i < CPL; ++i) acc[i] = fma(__ldg(B + c * KP + i), rc, acc[i]);
     }
-    store_row<T, CPL>(G + pix * KP + q * CPL, acc, T(1));
+    store_row_s<T, S, CPL>(G + pix * KP + q * CPL, acc, T(1));
 }
 
 __device__ __forceinline__ int sel3(int x, int y, int z, int axis)
@@ -319,8 +416,8 @@ __device__ __forceinline__ int sel3(int x, int y, int z, int axis)
 // geometry is thus computed once per voxel while a G row is still read as
 // one contiguous KP-float segment by the LG lanes together.  Per-projection
 // constants travel in the kernel's parameter space.
-template <typename T, int CPL, int KP, int LG, int NJ, int NK>
-__device__ __forceinline__ void adj_window(T (&acc)[LG][CPL], const T *__restrict__ Gq, int nk, int r0, T du0,
+template <typename T, typename S, int CPL, int KP, int LG, int NJ, int NK>
+__device__ __forceinline__ void adj_window(T (&acc)[LG][CPL], const S *__restrict__ Gq, int nk, int r0, T du0,
                                            T dv0, const AdjProj<T> &c, unsigned jmask, unsigned kmask)
 {
     // window origin row of every source voxel of the group (one shuffle each)
@@ -341,14 +438,14 @@ __device__ __forceinline__ void adj_window(T (&acc)[LG][CPL], const T *__restric
 #pragma unroll
             for (int src = 0; src < LG; ++src) {
                 const T ws = (LG == 1) ? w : __shfl_sync(0xffffffffu, w, src, LG);
-                if (ws != T(0)) fma_row<T, CPL>(acc[src], ws, Gq + (long long)(r0s[src] + off) * KP);
+                if (ws != T(0)) fma_row_s<T, S, CPL>(acc[src], ws, Gq + (long long)(r0s[src] + off) * KP);
             }
         }
     }
 }
 
-template <typename T, int CPL, int KP, int LG>
-__device__ __forceinline__ void adj_window_any(T (&acc)[LG][CPL], const T *__restrict__ Gq, int nj, int nk, int j0,
+template <typename T, typename S, int CPL, int KP, int LG>
+__device__ __forceinline__ void adj_window_any(T (&acc)[LG][CPL], const S *__restrict__ Gq, int nj, int nk, int j0,
                                             int k0, T du0, T dv0, const AdjProj<T> &c, bool valid)
 {
     for (int a = 0; a < c.nwj; ++a) {
@@ -365,15 +462,15 @@ __device__ __forceinline__ void adj_window_any(T (&acc)[LG][CPL], const T *__res
             for (int src = 0; src < LG; ++src) {
                 const T ws = (LG == 1) ? w : __shfl_sync(0xffffffffu, w, src, LG);
                 const int rs = (LG == 1) ? row : __shfl_sync(0xffffffffu, row, src, LG);
-                if (ws != T(0)) fma_row<T, CPL>(acc[src], ws, Gq + (long long)rs * KP);
+                if (ws != T(0)) fma_row_s<T, S, CPL>(acc[src], ws, Gq + (long long)rs * KP);
             }
         }
     }
 }
 
-template <typename T, int KP, int LG>
+template <typename T, typename S, int KP, int LG>
 __global__ void __launch_bounds__(kThreads, 3)
-k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const T *__restrict__ G, int nj, int nk, int nx,
+k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const S *__restrict__ G, int nj, int nk, int nx,
           int ny, int nz, int ty, int tz, T *__restrict__ gpad, int accumulate, T *__restrict__ gout, int K)
 {
     constexpr int CPL = KP / LG;
@@ -421,18 +518,18 @@ k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const T *__restrict__ 
                 km |= (unsigned)((unsigned)(k0 + a) < (unsigned)nk) << a;
             }
             if (!valid) { jm = 0; km = 0; }
-            const T *Gq = G + (size_t)si * gstride + q * CPL;
+            const S *Gq = G + (size_t)si * gstride + q * CPL;
             switch (c.shape) {
-            case 0x11: adj_window<T, CPL, KP, LG, 1, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            case 0x12: adj_window<T, CPL, KP, LG, 1, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            case 0x13: adj_window<T, CPL, KP, LG, 1, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            case 0x21: adj_window<T, CPL, KP, LG, 2, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            case 0x22: adj_window<T, CPL, KP, LG, 2, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            case 0x23: adj_window<T, CPL, KP, LG, 2, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            case 0x31: adj_window<T, CPL, KP, LG, 3, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            case 0x32: adj_window<T, CPL, KP, LG, 3, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            case 0x33: adj_window<T, CPL, KP, LG, 3, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            default: adj_window_any<T, CPL, KP, LG>(acc, Gq, nj, nk, j0, k0, du0, dv0, c, valid); break;
+            case 0x11: adj_window<T, S, CPL, KP, LG, 1, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x12: adj_window<T, S, CPL, KP, LG, 1, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x13: adj_window<T, S, CPL, KP, LG, 1, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x21: adj_window<T, S, CPL, KP, LG, 2, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x22: adj_window<T, S, CPL, KP, LG, 2, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x23: adj_window<T, S, CPL, KP, LG, 2, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x31: adj_window<T, S, CPL, KP, LG, 3, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x32: adj_window<T, S, CPL, KP, LG, 3, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x33: adj_window<T, S, CPL, KP, LG, 3, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            default: adj_window_any<T, S, CPL, KP, LG>(acc, Gq, nj, nk, j0, k0, du0, dv0, c, valid); break;
             }
         }
     }
@@ -460,7 +557,7 @@ k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const T *__restrict__ 
 
 // ------------------------------------------------------------ launchers
 
-template <typename T, int L>
+template <typename T, typename S, int L>
 cudaError_t launch_forward_L(tt_handle *h, T *Iout, const T *I, const T *W, bool grad)
 {
     constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K);
@@ -468,16 +565,17 @@ cudaError_t launch_forward_L(tt_handle *h, T *Iout, const T *I, const T *W, bool
     const int tiles_k = (h->nk + TK - 1) / TK, tiles_j = (h->nj + TJ - 1) / TJ;
     dim3 grid(tiles_k * tiles_j, h->S);
     const size_t smem = (size_t)h->CP * KP * sizeof(T);
-    const T *Bp = (const T *)h->Bp, *cpad = (const T *)h->cpad + h->cpad_origin * KP;
+    const T *Bp = (const T *)h->Bp;
+    const S *cpad = (const S *)h->cpad + h->cpad_origin * KP;
     cudaEvent_t ev;
     prof_begin(h, TT_KSLOT_FORWARD, &ev);
     if (grad) {
-        auto kern = k_forward<T, KP, LG, true>;
+        auto kern = k_forward<T, S, KP, LG, true>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<grid, kThreads, smem, h->stream>>>(h->geo, cpad, Bp, h->nj, h->nk, h->C, h->CP, tiles_k,
-                                                 nullptr, I, W, (T *)h->G, h->partials);
+                                                 nullptr, I, W, (S *)h->G, h->partials);
     } else {
-        auto kern = k_forward<T, KP, LG, false>;
+        auto kern = k_forward<T, S, KP, LG, false>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<grid, kThreads, smem, h->stream>>>(h->geo, cpad, Bp, h->nj, h->nk, h->C, h->CP, tiles_k,
                                                  Iout, nullptr, nullptr, nullptr, nullptr);
@@ -487,8 +585,8 @@ cudaError_t launch_forward_L(tt_handle *h, T *Iout, const T *I, const T *W, bool
     return e;
 }
 
-template <typename T, int L>
-cudaError_t launch_backcontract_L(tt_handle *h, const T *R, T *G)
+template <typename T, typename S, int L>
+cudaError_t launch_backcontract_L(tt_handle *h, const T *R)
 {
     constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K);
     constexpr int RAYS = kThreads / LG;
@@ -496,20 +594,21 @@ cudaError_t launch_backcontract_L(tt_handle *h, const T *R, T *G)
     const unsigned blocks = (unsigned)((npix + RAYS - 1) / RAYS);
     cudaEvent_t ev;
     prof_begin(h, TT_KSLOT_BACKCONTRACT, &ev);
-    k_backcontract<T, KP, LG><<<blocks, kThreads, 0, h->stream>>>((const T *)h->Bp, R, G, npix,
-                                                                 h->nj * h->nk, h->C, h->CP);
+    k_backcontract<T, S, KP, LG><<<blocks, kThreads, 0, h->stream>>>((const T *)h->Bp, R, (S *)h->G, npix,
+                                                                    h->nj * h->nk, h->C, h->CP);
     cudaError_t e = cudaGetLastError();
     prof_end(h, TT_KSLOT_BACKCONTRACT, ev);
     return e;
 }
 
-template <typename T, int L>
-cudaError_t launch_adjoint_L(tt_handle *h, const T *G, T *g)
+template <typename T, typename S, int L>
+cudaError_t launch_adjoint_L(tt_handle *h, T *g)
 {
     constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K);
     constexpr int BZ = 32, BY = 4, BX = (kThreads / 32) / BY;
     const int tx = (h->N[0] + BX - 1) / BX, ty = (h->N[1] + BY - 1) / BY, tz = (h->N[2] + BZ - 1) / BZ;
     const std::vector<AdjParams<T>> &chunks = adj_params<T>(h);
+    const S *G = (const S *)h->G;
     cudaError_t e = cudaSuccess;
     const int nchunk = (int)chunks.size();
     for (int ci = 0; ci < nchunk && e == cudaSuccess; ++ci) {
@@ -518,7 +617,7 @@ cudaError_t launch_adjoint_L(tt_handle *h, const T *G, T *g)
         const bool last = ci == nchunk - 1;
         cudaEvent_t ev;
         prof_begin(h, TT_KSLOT_ADJOINT, &ev);
-        k_adjoint<T, KP, LG><<<(unsigned)(tx * ty * tz), kThreads, 0, h->stream>>>(
+        k_adjoint<T, S, KP, LG><<<(unsigned)(tx * ty * tz), kThreads, 0, h->stream>>>(
             chunks[ci], ns, G + (size_t)s0 * h->nj * h->nk * KP, h->nj, h->nk, h->N[0], h->N[1], h->N[2], ty, tz,
             (T *)h->gpad, ci > 0 ? 1 : 0, last ? g : nullptr, h->K);
         e = cudaGetLastError();
@@ -527,16 +626,49 @@ cudaError_t launch_adjoint_L(tt_handle *h, const T *G, T *g)
     return e;
 }
 
-#define TT_DISPATCH_L(L, CALL)                       \
-    switch (L) {                                     \
-    case 0: return CALL(0);                          \
-    case 2: return CALL(2);                          \
-    case 4: return CALL(4);                          \
-    case 6: return CALL(6);                          \
-    case 8: return CALL(8);                          \
-    case 10: return CALL(10);                        \
-    case 12: return CALL(12);                        \
-    default: return cudaErrorInvalidValue;           \
+// Instantiates the three launchers of one (T, S) pair for every band limit.
+#define TT_INSTANTIATE_PROJECTORS(T, S)                                                        \
+    template <>                                                                                \
+    cudaError_t launch_forward<T, S>(tt_handle * h, T * Iout, const T *I, const T *W, bool grad) \
+    {                                                                                          \
+        switch (h->L) {                                                                        \
+        case 0: return launch_forward_L<T, S, 0>(h, Iout, I, W, grad);                         \
+        case 2: return launch_forward_L<T, S, 2>(h, Iout, I, W, grad);                         \
+        case 4: return launch_forward_L<T, S, 4>(h, Iout, I, W, grad);                         \
+        case 6: return launch_forward_L<T, S, 6>(h, Iout, I, W, grad);                         \
+        case 8: return launch_forward_L<T, S, 8>(h, Iout, I, W, grad);                         \
+        case 10: return launch_forward_L<T, S, 10>(h, Iout, I, W, grad);                       \
+        case 12: return launch_forward_L<T, S, 12>(h, Iout, I, W, grad);                       \
+        default: return cudaErrorInvalidValue;                                                 \
+        }                                                                                      \
+    }                                                                                          \
+    template <>                                                                                \
+    cudaError_t launch_backcontract<T, S>(tt_handle * h, const T *R)                           \
+    {                                                                                          \
+        switch (h->L) {                                                                        \
+        case 0: return launch_backcontract_L<T, S, 0>(h, R);                                   \
+        case 2: return launch_backcontract_L<T, S, 2>(h, R);                                   \
+        case 4: return launch_backcontract_L<T, S, 4>(h, R);                                   \
+        case 6: return launch_backcontract_L<T, S, 6>(h, R);                                   \
+        case 8: return launch_backcontract_L<T, S, 8>(h, R);                                   \
+        case 10: return launch_backcontract_L<T, S, 10>(h, R);                                 \
+        case 12: return launch_backcontract_L<T, S, 12>(h, R);                                 \
+        default: return cudaErrorInvalidValue;                                                 \
+        }                                                                                      \
+    }                                                                                          \
+    template <>                                                                                \
+    cudaError_t launch_adjoint<T, S>(tt_handle * h, T * g)                                     \
+    {                                                                                          \
+        switch (h->L) {                                                                        \
+        case 0: return launch_adjoint_L<T, S, 0>(h, g);                                        \
+        case 2: return launch_adjoint_L<T, S, 2>(h, g);                                        \
+        case 4: return launch_adjoint_L<T, S, 4>(h, g);                                        \
+        case 6: return launch_adjoint_L<T, S, 6>(h, g);                                        \
+        case 8: return launch_adjoint_L<T, S, 8>(h, g);                                        \
+        case 10: return launch_adjoint_L<T, S, 10>(h, g);                                      \
+        case 12: return launch_adjoint_L<T, S, 12>(h, g);                                      \
+        default: return cudaErrorInvalidValue;                                                 \
+        }                                                                                      \
     }
 
 }  // namespace tt

@@ -200,7 +200,7 @@ tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0, const void *I, co
     if (e == cudaSuccess) e = cudaMallocHost(&st->pinned, sizeof(double) * 8);
     if (e == cudaSuccess) e = cudaMemcpyAsync(st->x, c0, bytes, cudaMemcpyDeviceToDevice, h->stream);
     if (e != cudaSuccess) { free_state(st); return cuda_fail(e, "tt_lbfgs_create"); }
-    tt_status s = (h->prec == TT_F32)
+    tt_status s = (h->prec != TT_F64)
                       ? tt_grad_enqueue<float>(h, (const float *)st->x, (const float *)I, (const float *)W, (float *)st->g)
                       : tt_grad_enqueue<double>(h, (const double *)st->x, (const double *)I, (const double *)W,
                                                 (double *)st->g);
@@ -213,7 +213,7 @@ tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0, const void *I, co
 tt_status tt_lbfgs_step(tt_handle *h, tt_lbfgs *st, void *c_out, double *loss_host, int *n_evals_host)
 {
     if (!h || !st || st->h != h) { set_error("tt_lbfgs_step: state does not belong to this handle"); return TT_INVALID_ARG; }
-    tt_status s = (h->prec == TT_F32) ? lbfgs_step<float>(st, loss_host, n_evals_host)
+    tt_status s = (h->prec != TT_F64) ? lbfgs_step<float>(st, loss_host, n_evals_host)
                                       : lbfgs_step<double>(st, loss_host, n_evals_host);
     if (c_out && (s == TT_OK || s == TT_LINESEARCH_FAILED)) {
         cudaError_t e = cudaMemcpyAsync(c_out, st->x, h->esize() * st->n, cudaMemcpyDeviceToDevice, h->stream);
@@ -234,7 +234,8 @@ tt_status tt_lbfgs_get(tt_handle *h, tt_lbfgs *st, void *c_dev, void *g_dev, dou
 
 tt_status tt_lbfgs_destroy(tt_lbfgs *st)
 {
-    if (st && st->h) cudaStreamSynchronize(st->h->stream);
+    // Does not touch st->h: the handle may already be destroyed.  cudaFree
+    // waits for the device, so no pending work of the state is cut short.
     free_state(st);
     return TT_OK;
 }

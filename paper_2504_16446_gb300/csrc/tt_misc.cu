@@ -9,8 +9,16 @@ namespace tt {
 
 // Interior of the padded volume: cpad[x+2][y+2][z+2][i] = c[x][y][z][i] for
 // i < K, 0 for K <= i < KP (the two-voxel border is zeroed once at creation).
-template <typename T>
-__global__ void k_pack(const T *__restrict__ c, T *__restrict__ cpad, int nx, int ny, int nz, int K, int KP)
+template <typename T, typename S>
+__device__ __forceinline__ S to_storage(T x)
+{
+    if constexpr (std::is_same<S, __nv_bfloat16>::value) return __float2bfloat16_rn(x);
+    else if constexpr (std::is_same<S, __half>::value) return __float2half_rn(x);
+    else return x;
+}
+
+template <typename T, typename S>
+__global__ void k_pack(const T *__restrict__ c, S *__restrict__ cpad, int nx, int ny, int nz, int K, int KP)
 {
     const long long n = (long long)nx * ny * nz * KP;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
@@ -19,7 +27,7 @@ __global__ void k_pack(const T *__restrict__ c, T *__restrict__ cpad, int nx, in
         const int i = (int)(t - v * KP);
         const int z = (int)(v % nz), y = (int)((v / nz) % ny), x = (int)(v / ((long long)nz * ny));
         const long long o = (((long long)(x + 2) * (ny + 4) + (y + 2)) * (nz + 4) + (z + 2)) * KP + i;
-        cpad[o] = i < K ? __ldg(c + v * K + i) : T(0);
+        cpad[o] = to_storage<T, S>(i < K ? __ldg(c + v * K + i) : T(0));
     }
 }
 
@@ -43,13 +51,13 @@ static unsigned grid_for(long long n, int per_block = 256)
     return (unsigned)b;
 }
 
-template <typename T>
+template <typename T, typename S>
 cudaError_t launch_pack(tt_handle *h, const T *c)
 {
     cudaEvent_t ev;
     prof_begin(h, TT_KSLOT_PACK, &ev);
-    k_pack<T><<<grid_for(h->nvox() * h->KP), 256, 0, h->stream>>>(c, (T *)h->cpad, h->N[0], h->N[1], h->N[2], h->K,
-                                                                h->KP);
+    k_pack<T, S><<<grid_for(h->nvox() * h->KP), 256, 0, h->stream>>>(c, (S *)h->cpad, h->N[0], h->N[1], h->N[2],
+                                                                   h->K, h->KP);
     cudaError_t e = cudaGetLastError();
     prof_end(h, TT_KSLOT_PACK, ev);
     return e;
@@ -66,8 +74,10 @@ cudaError_t launch_unpack(tt_handle *h, const T *gpad, T *g)
     return e;
 }
 
-template cudaError_t launch_pack<float>(tt_handle *, const float *);
-template cudaError_t launch_pack<double>(tt_handle *, const double *);
+template cudaError_t launch_pack<float, float>(tt_handle *, const float *);
+template cudaError_t launch_pack<double, double>(tt_handle *, const double *);
+template cudaError_t launch_pack<float, __nv_bfloat16>(tt_handle *, const float *);
+template cudaError_t launch_pack<float, __half>(tt_handle *, const float *);
 template cudaError_t launch_unpack<float>(tt_handle *, const float *, float *);
 template cudaError_t launch_unpack<double>(tt_handle *, const double *, double *);
 
@@ -116,9 +126,16 @@ __global__ void k_axpby(T *__restrict__ y, const T *__restrict__ x, long long n,
 {
     const T a = (T)(ha * (da ? da[0] : 1.0));
     const T b = (T)hb;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x)
-        y[t] = fma(a, x[t], b * y[t]);
+    // b == 0 overwrites y without reading it (y may hold NaN bit patterns).
+    if (hb == 0.0) {
+        for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+             t += (long long)gridDim.x * blockDim.x)
+            y[t] = a * x[t];
+    } else {
+        for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+             t += (long long)gridDim.x * blockDim.x)
+            y[t] = fma(a, x[t], b * y[t]);
+    }
 }
 
 template <typename T>

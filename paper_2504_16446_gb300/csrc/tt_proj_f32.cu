@@ -1,30 +1,7 @@
-// tt_proj_f32.cu -- float instantiations of the projector kernels.
+// tt_proj_f32.cu -- projector kernels with float arithmetic and float storage of
+// the coefficient volume and of the back-contracted residual.
 #include "tt_kernels.cuh"
 
 namespace tt {
-
-template <>
-cudaError_t launch_forward<float>(tt_handle *h, float *Iout, const float *I, const float *W, bool grad)
-{
-#define TT_CALL(L) launch_forward_L<float, L>(h, Iout, I, W, grad)
-    TT_DISPATCH_L(h->L, TT_CALL)
-#undef TT_CALL
-}
-
-template <>
-cudaError_t launch_backcontract<float>(tt_handle *h, const float *R, float *G)
-{
-#define TT_CALL(L) launch_backcontract_L<float, L>(h, R, G)
-    TT_DISPATCH_L(h->L, TT_CALL)
-#undef TT_CALL
-}
-
-template <>
-cudaError_t launch_adjoint<float>(tt_handle *h, const float *G, float *g)
-{
-#define TT_CALL(L) launch_adjoint_L<float, L>(h, G, g)
-    TT_DISPATCH_L(h->L, TT_CALL)
-#undef TT_CALL
-}
-
+TT_INSTANTIATE_PROJECTORS(float, float)
 }  // namespace tt

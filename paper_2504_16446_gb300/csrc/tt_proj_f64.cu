@@ -1,30 +1,7 @@
-// tt_proj_f64.cu -- double instantiations of the projector kernels.
+// tt_proj_f64.cu -- projector kernels with double arithmetic and double storage of
+// the coefficient volume and of the back-contracted residual.
 #include "tt_kernels.cuh"
 
 namespace tt {
-
-template <>
-cudaError_t launch_forward<double>(tt_handle *h, double *Iout, const double *I, const double *W, bool grad)
-{
-#define TT_CALL(L) launch_forward_L<double, L>(h, Iout, I, W, grad)
-    TT_DISPATCH_L(h->L, TT_CALL)
-#undef TT_CALL
-}
-
-template <>
-cudaError_t launch_backcontract<double>(tt_handle *h, const double *R, double *G)
-{
-#define TT_CALL(L) launch_backcontract_L<double, L>(h, R, G)
-    TT_DISPATCH_L(h->L, TT_CALL)
-#undef TT_CALL
-}
-
-template <>
-cudaError_t launch_adjoint<double>(tt_handle *h, const double *G, double *g)
-{
-#define TT_CALL(L) launch_adjoint_L<double, L>(h, G, g)
-    TT_DISPATCH_L(h->L, TT_CALL)
-#undef TT_CALL
-}
-
+TT_INSTANTIATE_PROJECTORS(double, double)
 }  // namespace tt

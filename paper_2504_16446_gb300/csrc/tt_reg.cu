@@ -129,7 +129,10 @@ static tt_status tv_impl(tt_handle *h, const T *c, double delta, T *grad, double
 static tt_status reg_check(const tt_handle *h, tt_precision want, const void *c, const void *grad, const double *value)
 {
     if (!h) { set_error("null handle"); return TT_INVALID_ARG; }
-    if (h->prec != want) { set_error("handle precision does not match the entry point"); return TT_INVALID_ARG; }
+    if ((h->prec == TT_F64) != (want == TT_F64)) {
+        set_error("handle precision does not match the entry point");
+        return TT_INVALID_ARG;
+    }
     if (!c || !value || (reinterpret_cast<uintptr_t>(c) & 15u) || (grad && (reinterpret_cast<uintptr_t>(grad) & 15u))) {
         set_error("regulariser: c and value must be non-null, device pointers 16-byte aligned");
         return TT_INVALID_ARG;

@@ -18,7 +18,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libtt.so")
 
 TT_OK, TT_INVALID_ARG, TT_UNSUPPORTED, TT_OUT_OF_MEMORY, TT_NONFINITE, TT_LINESEARCH_FAILED, TT_CUDA_ERROR = range(7)
-TT_F32, TT_F64 = 0, 1
+TT_F32, TT_F64, TT_BF16, TT_F16 = 0, 1, 2, 3
+PRECISIONS = {"f32": TT_F32, "f64": TT_F64, "bf16": TT_BF16, "f16": TT_F16}
 KSLOTS = ["pack", "forward", "backcontract", "adjoint", "unpack", "reduce", "basis", "vector"]
 
 _lock = threading.Lock()
@@ -148,14 +149,15 @@ class Handle:
 
     ``setup`` is any object with the fields of ``synth.Setup`` (shape, nj, nk,
     ell_max, inner_angle, outer_angle, seg_start, seg_end, j_offset, k_offset,
-    two_theta, a, b).  precision: "f32" or "f64".
+    two_theta, a, b).  precision: "f32", "f64", or "bf16" / "f16" (float API,
+    2-byte storage of the volume and of the back-contracted residual).
     """
 
     def __init__(self, setup, precision: str = "f32", stream=None, frame=None):
         self.lib = load()
         self.setup = setup
         self.precision = precision
-        self.dtype = {"f32": torch.float32, "f64": torch.float64}[precision]
+        self.dtype = torch.float64 if precision == "f64" else torch.float32
         self._arrays = [np.ascontiguousarray(a, dtype=np.float64) for a in (
             setup.inner_angle, setup.outer_angle, setup.j_offset, setup.k_offset, setup.seg_start, setup.seg_end)]
         P = _Problem()
@@ -172,7 +174,7 @@ class Handle:
             setattr(P.frame, name, (ctypes.c_double * 3)(*[float(x) for x in fr[name]]))
         self._prob = P
         h = _P()
-        _check(self.lib.tt_create(ctypes.byref(P), TT_F32 if precision == "f32" else TT_F64,
+        _check(self.lib.tt_create(ctypes.byref(P), PRECISIONS[precision],
                                   _stream_ptr(stream), ctypes.byref(h)), "tt_create")
         self._h = h
         self.K = num_coeffs(setup.ell_max)
@@ -240,8 +242,8 @@ class Handle:
     def gradient_residual_host(self, c: np.ndarray, I: np.ndarray, W=None, g_out=None):
         """End-to-end call on HOST arrays (float32); returns (loss, g)."""
         self._sync_stream()
-        if self.precision != "f32":
-            raise TypeError("host entry point is FP32 only")
+        if self.precision == "f64":
+            raise TypeError("the host entry point takes float arrays")
         for name, a, shp in (("c", c, self.volume_shape), ("I", I, self.data_shape)):
             if a.dtype != np.float32 or a.shape != shp or not a.flags["C_CONTIGUOUS"]:
                 raise ValueError(f"{name} must be C-contiguous float32 of shape {shp}")
