@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-loss", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the per-precision timings of the 64^3 and 128^3 workloads")
     ap.add_argument("--ttl-ref-iters", type=int, default=300,
                     help="L-BFGS iterations of the reference solve that defines L*")
     ap.add_argument("--cpu-sample-evals", type=float, default=4.0,
@@ -196,10 +198,8 @@ def make_inputs(st, torch, tt, synth):
     return h, c, I, W
 
 
-def time_to_loss(h, I, W, torch, tt, ref_iters: int, target: float = 1e-3):
-    """Plain FP32 L-BFGS from zero: wall time, iterations and gradient
-    evaluations until the excess loss (L - L*) / (L0 - L*) <= target, where
-    L* is the loss after ref_iters iterations of the same solver."""
+def reference_loss(h, I, W, torch, tt, ref_iters: int):
+    """(L0, L*) of the plain FP32 solve: L* = loss after ref_iters L-BFGS iterations."""
     z = torch.zeros(h.volume_shape, dtype=torch.float32, device="cuda")
     ref = tt.LBFGS(h, z, I, W, m=10)
     L0 = ref.loss
@@ -209,6 +209,17 @@ def time_to_loss(h, I, W, torch, tt, ref_iters: int, target: float = 1e-3):
             break
     Lstar = ref.loss
     ref.close()
+    return L0, Lstar
+
+
+def time_to_loss(h, I, W, torch, tt, ref_iters: int, target: float = 1e-3, L0_Lstar=None):
+    """L-BFGS from zero on handle h: wall time, iterations and gradient
+    evaluations until the excess loss (L - L*) / (L0 - L*) <= target, where
+    L0, L* belong to the plain FP32 solve (L* = loss after ref_iters
+    iterations).  The loss of a reduced-precision handle is its own FP64 sum
+    of its residuals."""
+    L0, Lstar = L0_Lstar if L0_Lstar else reference_loss(h, I, W, torch, tt, ref_iters)
+    z = torch.zeros(h.volume_shape, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     opt = tt.LBFGS(h, z, I, W, m=10)
@@ -226,6 +237,44 @@ def time_to_loss(h, I, W, torch, tt, ref_iters: int, target: float = 1e-3):
     return {"seconds": dt, "iterations": iters, "evals": evals, "reached": bool(reached),
             "criterion": f"(L - L*)/(L0 - L*) <= {target:g}, L* = loss after {ref_iters} L-BFGS iterations (m=10)",
             "L0": L0, "L_star": Lstar}
+
+
+def measure_forms(torch, tt, synth, flush, steps: int = 20):
+    """ms per gradient evaluation of the FP32, bfloat16- and float16-storage
+    forms on the 64^3 (l_max 4) and 128^3 (l_max 8, 240 x 128^2 x 8) workloads;
+    random O(1) volume and data, L2 flushed between evaluations."""
+    res = {}
+    for wl in ("ell64", "ell128"):
+        st = synth.workload(wl)
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(7)
+        c = torch.randn(st.volume_shape, device="cuda", generator=gen)
+        I = torch.rand(st.data_shape, device="cuda", generator=gen) * st.shape[0]
+        g = torch.empty_like(c)
+        row = {}
+        for prec in ("f32", "bf16", "f16"):
+            h = tt.Handle(st, prec)
+            for _ in range(3):
+                h.gradient_residual(c, I, None, out=g)
+            h.profile(True)
+            h.profile_reset()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tot = 0.0
+            for _ in range(steps):
+                flush.zero_()
+                ev0.record()
+                h.gradient_residual(c, I, None, out=g)
+                ev1.record()
+                ev1.synchronize()
+                tot += ev0.elapsed_time(ev1)
+            p = h.profile_read()
+            row[prec] = {"ms_per_eval": tot / steps,
+                         "forward_ms": p["forward"][0] / max(1, p["forward"][1]),
+                         "adjoint_ms": p["adjoint"][0] / max(1, p["adjoint"][1])}
+            h.close()
+        row["workload"] = f"{st.shape[0]}^3, l_max {st.ell_max}, {st.S} x {st.nj}x{st.nk} x {st.C}"
+        res[wl] = row
+    return res
 
 
 def run_ours(args):
@@ -341,7 +390,13 @@ def run_ours(args):
         "loss": losses[-1],
     }
     if not args.no_time_to_loss:
-        out["time_to_loss"] = {"plain_f32": time_to_loss(h, I, W, torch, tt, args.ttl_ref_iters)}
+        ref = reference_loss(h, I, W, torch, tt, args.ttl_ref_iters)
+        out["time_to_loss"] = {"plain_f32": time_to_loss(h, I, W, torch, tt, args.ttl_ref_iters, L0_Lstar=ref)}
+        hb = tt.Handle(st, "bf16")
+        out["time_to_loss"]["bf16"] = time_to_loss(hb, I, W, torch, tt, args.ttl_ref_iters, L0_Lstar=ref)
+        hb.close()
+    if not args.no_forms:
+        out["forms"] = measure_forms(torch, tt, synth, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, dt, sample = cpu_oracle_rate(st, c.cpu().numpy(), I.cpu().numpy(), W.cpu().numpy(),
                                            args.cpu_sample_evals)

@@ -228,7 +228,7 @@ tt_status validate(const tt_problem *P)
     if (P->nx < 1 || P->ny < 1 || P->nz < 1) return invalid("volume shape must be >= 1 in every axis");
     if ((long long)P->nx * P->ny * P->nz > (1LL << 31) / 128) return invalid("volume too large");
     if (P->nj < 1 || P->nk < 1) return invalid("nj, nk must be >= 1");
-    if (P->n_proj < 1) return invalid("n_proj must be >= 1");
+    if (P->n_proj < 1 || P->n_proj > 65535) return invalid("n_proj must be in [1, 65535]");
     if (P->ell_max < 0 || (P->ell_max & 1)) return invalid("ell_max must be even and >= 0");
     if (P->n_seg < 1 || P->n_seg > kMaxSeg) return invalid("n_seg must be in [1, 64]");
     if (!P->inner_angle || !P->outer_angle || !P->seg_start || !P->seg_end)

@@ -275,7 +275,7 @@ template <typename T, typename S, int KP, int LG, bool GRAD>
 __global__ void __launch_bounds__(kThreads)
 k_forward(const ProjGeom *__restrict__ geo, const S *__restrict__ cpad /* interior origin */,
           const T *__restrict__ Bp,
-          int nj, int nk, int C, int CP, int tiles_k,
+          int nj, int nk, int C, int CP, int tiles_k, int slab_order,
           T *__restrict__ Iout, const T *__restrict__ Id, const T *__restrict__ Wd,
           S *__restrict__ G, double *__restrict__ partials)
 {
@@ -287,8 +287,15 @@ k_forward(const ProjGeom *__restrict__ geo, const S *__restrict__ cpad /* interi
     T *Bs = reinterpret_cast<T *>(smem_raw);   // [CP][KP]
     __shared__ double red[kThreads / 32];
 
-    const int s = blockIdx.y;
-    const int tj = blockIdx.x / tiles_k, tk = blockIdx.x % tiles_k;
+    // CTA order.  slab_order == 0: all tiles of one projection, projection by
+    // projection (gridDim = (tiles_k * tiles_j, S)).  slab_order == 1: k tile
+    // fastest, then projection, then j tile (gridDim = (tiles_k * S, tiles_j)),
+    // so that the CTAs in flight march the same few detector rows of many
+    // projections -- for rotations about the j axis the same y-slab of the
+    // volume, which then stays in L2 when the whole volume does not fit.
+    int tk, s, tj;
+    if (slab_order) { tk = blockIdx.x % tiles_k; s = blockIdx.x / tiles_k; tj = blockIdx.y; }
+    else { s = blockIdx.y; tj = blockIdx.x / tiles_k; tk = blockIdx.x % tiles_k; }
     const int r = threadIdx.x / LG, q = threadIdx.x % LG;
     const int j = tj * TJ + r / TK, k = tk * TK + r % TK;
     const bool valid = (j < nj) && (k < nk);
@@ -563,7 +570,10 @@ cudaError_t launch_forward_L(tt_handle *h, T *Iout, const T *I, const T *W, bool
     constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K);
     constexpr int RAYS = kThreads / LG, TK = 8, TJ = RAYS / TK;
     const int tiles_k = (h->nk + TK - 1) / TK, tiles_j = (h->nj + TJ - 1) / TJ;
-    dim3 grid(tiles_k * tiles_j, h->S);
+    // slab order once the padded volume would take more than half of L2
+    const long long vol_bytes = (long long)(h->N[0] + 4) * (h->N[1] + 4) * (h->N[2] + 4) * KP * sizeof(S);
+    const int slab = vol_bytes > (64LL << 20) ? 1 : 0;
+    const dim3 grid = slab ? dim3(tiles_k * h->S, tiles_j) : dim3(tiles_k * tiles_j, h->S);
     const size_t smem = (size_t)h->CP * KP * sizeof(T);
     const T *Bp = (const T *)h->Bp;
     const S *cpad = (const S *)h->cpad + h->cpad_origin * KP;
@@ -572,12 +582,12 @@ cudaError_t launch_forward_L(tt_handle *h, T *Iout, const T *I, const T *W, bool
     if (grad) {
         auto kern = k_forward<T, S, KP, LG, true>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<grid, kThreads, smem, h->stream>>>(h->geo, cpad, Bp, h->nj, h->nk, h->C, h->CP, tiles_k,
+        kern<<<grid, kThreads, smem, h->stream>>>(h->geo, cpad, Bp, h->nj, h->nk, h->C, h->CP, tiles_k, slab,
                                                  nullptr, I, W, (S *)h->G, h->partials);
     } else {
         auto kern = k_forward<T, S, KP, LG, false>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<grid, kThreads, smem, h->stream>>>(h->geo, cpad, Bp, h->nj, h->nk, h->C, h->CP, tiles_k,
+        kern<<<grid, kThreads, smem, h->stream>>>(h->geo, cpad, Bp, h->nj, h->nk, h->C, h->CP, tiles_k, slab,
                                                  Iout, nullptr, nullptr, nullptr, nullptr);
     }
     cudaError_t e = cudaGetLastError();
