@@ -205,6 +205,49 @@ tt_status tt_lbfgs_get(tt_handle *h, tt_lbfgs *st, void *c_dev, void *g_dev, dou
 /* Frees the state; valid before or after tt_destroy of its handle. */
 tt_status tt_lbfgs_destroy(tt_lbfgs *st);
 
+/* Learned warm start: a 3-D convolutional network (4 layers of 3x3x3
+ * convolutions, k_in -> 32 -> 32 -> 32 -> k_out channels, ReLU between
+ * layers, no biases; "same" zero padding) that maps the first back-projected
+ * gradient of a reconstruction to a starting coefficient volume.  The paper's
+ * outlook proposes simulated data for training machine-learning models; the
+ * network and its training are this library's.  Weights are kept in FP32
+ * (Adam), activations in bfloat16, convolutions run on the tensor cores with
+ * FP32 accumulation.  Volumes are [nx][ny][nz][channels] FP32 device arrays.
+ * Because the network is bias-free and ReLU is positively homogeneous,
+ * y = out_scale * net(x / in_scale) is exactly equivariant to the scale of x.
+ *   w_host: HOST array of tt_wsnet_num_weights(k_in, k_out) floats, layer by
+ *   layer, each [3][3][3][c_out][c_in] (tap index (dx+1, dy+1, dz+1)).
+ *   tt_wsnet_forward:    y = out_scale * net(x / in_scale).
+ *   tt_wsnet_gradient:   loss = mean((net(x/in_scale) - target/out_scale)^2) over
+ *                        voxels and k_out channels, and its weight gradient
+ *                        into grad_host (may be NULL); synchronises.
+ *   tt_wsnet_train_step: the same loss, then one Adam step (beta 0.9, 0.999,
+ *                        eps 1e-8, learning rate lr); synchronises. */
+typedef struct tt_wsnet tt_wsnet;
+int tt_wsnet_num_weights(int k_in, int k_out);
+tt_status tt_wsnet_create(int k_in, int k_out, const float *w_host, void *stream, tt_wsnet **out);
+tt_status tt_wsnet_destroy(tt_wsnet *net);
+tt_status tt_wsnet_set_stream(tt_wsnet *net, void *stream);
+tt_status tt_wsnet_forward(tt_wsnet *net, int nx, int ny, int nz, const float *x_dev, double in_scale,
+                           double out_scale, float *y_dev);
+tt_status tt_wsnet_gradient(tt_wsnet *net, int nx, int ny, int nz, const float *x_dev, const float *target_dev,
+                            double in_scale, double out_scale, float *grad_host, double *loss_host);
+tt_status tt_wsnet_train_step(tt_wsnet *net, int nx, int ny, int nz, const float *x_dev, const float *target_dev,
+                              double in_scale, double out_scale, double lr, double *loss_host);
+tt_status tt_wsnet_get_weights(tt_wsnet *net, float *w_host);
+/* The network's two convolution kernels on their own (bfloat16 operands as
+ * raw 16-bit words, device pointers, enqueued on stream):
+ *   tt_conv3d_bf16:       y[v][co] = sum_t sum_ci x[v + d_t][ci] w[t][co][ci]
+ *                         (x [nvox][cin], w [27][cout][cin], y float [nvox][cout];
+ *                         relu must be 0);
+ *   tt_conv3d_wgrad_bf16: dw[t][co][ci] += sum_v dy[v][co] x[v + d_t][ci]
+ *                         (dy [nvox][cout], dw float [27][cout][cin]).
+ * cin, cout in {16, 32}. */
+tt_status tt_conv3d_bf16(int nx, int ny, int nz, int cin, int cout, const void *x_dev, const void *w_dev, int relu,
+                         float *y_dev, void *stream);
+tt_status tt_conv3d_wgrad_bf16(int nx, int ny, int nz, int cin, int cout, const void *x_dev, const void *dy_dev,
+                               float *dw_dev, void *stream);
+
 /* Phantom helper: SH coefficients of zonal functions rotated to unit axes n,
  * c_lm = a_l sqrt(4 pi/(2l+1)) Y_lm(n) (addition theorem).  dirs_dev [n][3],
  * amps_dev [n][ell_max/2+1], c_dev [n][K], FP32, device, on stream. */

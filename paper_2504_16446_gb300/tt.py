@@ -85,6 +85,19 @@ SIGNATURES = {
     "tt_lbfgs_step": (ctypes.c_int, [_P, _P, _P, _D, ctypes.POINTER(ctypes.c_int)]),
     "tt_lbfgs_get": (ctypes.c_int, [_P, _P, _P, _P, _D]),
     "tt_lbfgs_destroy": (ctypes.c_int, [_P]),
+    "tt_wsnet_num_weights": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    "tt_wsnet_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(_P)]),
+    "tt_wsnet_destroy": (ctypes.c_int, [_P]),
+    "tt_wsnet_set_stream": (ctypes.c_int, [_P, _P]),
+    "tt_wsnet_forward": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_double,
+                                        ctypes.c_double, _P]),
+    "tt_wsnet_gradient": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_double,
+                                         ctypes.c_double, _P, _D]),
+    "tt_wsnet_train_step": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, _D]),
+    "tt_wsnet_get_weights": (ctypes.c_int, [_P, _P]),
+    "tt_conv3d_bf16": (ctypes.c_int, [ctypes.c_int] * 5 + [_P, _P, ctypes.c_int, _P, _P]),
+    "tt_conv3d_wgrad_bf16": (ctypes.c_int, [ctypes.c_int] * 5 + [_P, _P, _P, _P]),
     "tt_zonal_to_sh": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, _P, _P, _P, _P]),
     "tt_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "tt_profile_read": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_longlong)]),
@@ -353,3 +366,89 @@ def zonal_to_sh(ell_max: int, dirs: torch.Tensor, amps: torch.Tensor) -> torch.T
                               _dptr(a, torch.float32, (n, ell_max // 2 + 1), "amps"),
                               ctypes.c_void_p(c.data_ptr()), _stream_ptr()), "tt_zonal_to_sh")
     return c
+
+
+class WarmStartNet:
+    """The learned warm start (tt_wsnet_*): 4 layers of 3x3x3 convolutions,
+    k_in -> 32 -> 32 -> 32 -> k_out, ReLU between layers, no biases."""
+
+    HIDDEN = 32
+
+    def __init__(self, k_in: int, k_out: int, weights: np.ndarray | None = None, seed: int = 0):
+        self.lib = load()
+        self.k_in, self.k_out = int(k_in), int(k_out)
+        n = self.lib.tt_wsnet_num_weights(self.k_in, self.k_out)
+        if n <= 0:
+            raise ValueError("k_in, k_out must be in [1, 16]")
+        if weights is None:
+            weights = self.he_init(self.k_in, self.k_out, seed)
+        w = np.ascontiguousarray(weights, dtype=np.float32).ravel()
+        if w.size != n:
+            raise ValueError(f"expected {n} weights, got {w.size}")
+        h = _P()
+        _check(self.lib.tt_wsnet_create(self.k_in, self.k_out, w.ctypes.data_as(_P), _stream_ptr(),
+                                        ctypes.byref(h)), "tt_wsnet_create")
+        self._h = h
+
+    @staticmethod
+    def layer_shapes(k_in, k_out):
+        H = WarmStartNet.HIDDEN
+        return [(3, 3, 3, H, k_in), (3, 3, 3, H, H), (3, 3, 3, H, H), (3, 3, 3, k_out, H)]
+
+    @staticmethod
+    def he_init(k_in, k_out, seed):
+        """He-normal initial weights (seeded), flattened layer by layer."""
+        rng = np.random.default_rng(seed)
+        parts = [rng.normal(0.0, np.sqrt(2.0 / (27 * shp[4])), shp).astype(np.float32)
+                 for shp in WarmStartNet.layer_shapes(k_in, k_out)]
+        return np.concatenate([p.ravel() for p in parts])
+
+    def _sync(self):
+        _check(self.lib.tt_wsnet_set_stream(self._h, _stream_ptr()), "tt_wsnet_set_stream")
+
+    def forward(self, x: torch.Tensor, in_scale: float, out_scale: float | None = None) -> torch.Tensor:
+        """out_scale * net(x / in_scale) (out_scale defaults to in_scale)."""
+        self._sync()
+        nx, ny, nz, _ = x.shape
+        y = torch.empty((nx, ny, nz, self.k_out), dtype=torch.float32, device=x.device)
+        _check(self.lib.tt_wsnet_forward(self._h, nx, ny, nz, _dptr(x, torch.float32, (nx, ny, nz, self.k_in), "x"),
+                                         float(in_scale), float(in_scale if out_scale is None else out_scale),
+                                         ctypes.c_void_p(y.data_ptr())), "tt_wsnet_forward")
+        return y
+
+    def gradient(self, x, target, in_scale, out_scale=None):
+        self._sync()
+        nx, ny, nz, _ = x.shape
+        g = np.empty(self.lib.tt_wsnet_num_weights(self.k_in, self.k_out), np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(self.lib.tt_wsnet_gradient(self._h, nx, ny, nz, _dptr(x, torch.float32, (nx, ny, nz, self.k_in), "x"),
+                                          _dptr(target, torch.float32, (nx, ny, nz, self.k_out), "target"),
+                                          float(in_scale), float(in_scale if out_scale is None else out_scale),
+                                          g.ctypes.data_as(_P), ctypes.byref(loss)), "tt_wsnet_gradient")
+        return loss.value, g
+
+    def train_step(self, x, target, in_scale, lr, out_scale=None):
+        self._sync()
+        nx, ny, nz, _ = x.shape
+        loss = ctypes.c_double(0.0)
+        _check(self.lib.tt_wsnet_train_step(self._h, nx, ny, nz, _dptr(x, torch.float32, (nx, ny, nz, self.k_in), "x"),
+                                            _dptr(target, torch.float32, (nx, ny, nz, self.k_out), "target"),
+                                            float(in_scale), float(in_scale if out_scale is None else out_scale),
+                                            float(lr), ctypes.byref(loss)), "tt_wsnet_train_step")
+        return loss.value
+
+    def weights(self) -> np.ndarray:
+        w = np.empty(self.lib.tt_wsnet_num_weights(self.k_in, self.k_out), np.float32)
+        _check(self.lib.tt_wsnet_get_weights(self._h, w.ctypes.data_as(_P)), "tt_wsnet_get_weights")
+        return w
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.tt_wsnet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
