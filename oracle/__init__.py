@@ -289,3 +289,4 @@ def zonal_to_sh(ell_max: int, dirs, amps) -> np.ndarray:
 
 
 from .lbfgs import LBFGS  # noqa: E402  (numpy two-loop L-BFGS on top of the above)
+from .sirt import MITRA, sirt_weights  # noqa: E402  (SIRT-preconditioned solver)
