@@ -1,0 +1,179 @@
+"""Learned warm start for the L-BFGS reconstruction (library side).
+
+A small 3-D convolutional network (tt.WarmStartNet: 4 layers of 3x3x3
+convolutions, 15 -> 32 -> 32 -> 32 -> 15 channels, bfloat16 activations,
+tensor-core kernels) maps the first back-projected gradient g0 = grad L(0) of
+a reconstruction to a starting coefficient volume.  It is trained on
+phantoms paired with their plain L-BFGS reconstructions, which the plain
+method itself produces.  The zero-start plain solve remains the fallback
+and the judge: the warm start is used only if its loss is below L(0).
+
+Scale: the network is bias-free and ReLU is positively homogeneous, so the
+input is normalised by its RMS and the output scale is fixed at inference by
+the exact minimiser of the loss along the predicted direction u:
+L(alpha u) = alpha^2 |Au|^2 - 2 alpha <Au, I> + |I|^2 (W = 1), whose three
+coefficients follow from the library's loss at 0, u and 2u.
+
+Running this module (``python -m paper_2504_16446_gb300.warmstart``) trains
+on the 64^3 ellipsoid workload and tests on held-out 128^3 phantoms (l_max 4,
+240 projections of 128 x 128 x 16 segments), printing one JSON line with the
+iterations and wall time to a 1e-3 excess loss for the zero-start FP32
+solve, the warm-started FP32 solve and the warm-started bfloat16-storage
+solve.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import synth, tt
+
+
+def phantom_data(h: tt.Handle, st, n_ell: int, seed: int, mean_counts: float = 1e4):
+    """(I, c_true): Poisson data of a seeded ellipsoid phantom (GPU forward model)."""
+    ph = synth.ellipsoid_phantom(st.shape[0], st.ell_max, n_ell, seed)
+    dirs = torch.as_tensor(ph.dirs.reshape(-1, 3), dtype=torch.float32, device="cuda")
+    amps = torch.as_tensor(ph.amps.reshape(-1, st.ell_max // 2 + 1), dtype=torch.float32, device="cuda")
+    c_true = tt.zonal_to_sh(st.ell_max, dirs, amps).reshape(st.volume_shape).contiguous()
+    clean = h.project(c_true)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    scale = mean_counts / float(clean.mean())
+    I = (torch.poisson(clean.clamp(min=0) * scale, generator=gen) / scale).contiguous()
+    return I, c_true
+
+
+def plain_solve(h: tt.Handle, I, iters: int, c0=None):
+    """Plain FP32 L-BFGS (m = 10) from c0 (zero by default): (c, loss)."""
+    z = torch.zeros(h.volume_shape, dtype=torch.float32, device="cuda") if c0 is None else c0
+    opt = tt.LBFGS(h, z, I, None, m=10)
+    for _ in range(iters):
+        _, _, st = opt.step()
+        if st != tt.TT_OK:
+            break
+    c = opt.get()[0]
+    loss = opt.loss
+    opt.close()
+    return c, loss
+
+
+def warm_start(net: tt.WarmStartNet, h: tt.Handle, I, g0, L0: float):
+    """(c0, loss): alpha * net(g0 / rms(g0)) with the loss-minimising alpha, or
+    zero when that does not beat L(0)."""
+    s_in = float(g0.pow(2).mean().sqrt())
+    u = net.forward(g0, s_in, 1.0).contiguous()
+    L1, _ = h.gradient_residual(u, I, None, want_grad=False)
+    L2, _ = h.gradient_residual((2.0 * u).contiguous(), I, None, want_grad=False)
+    quad = 0.5 * (L2 - 2.0 * L1 + L0)          # |Au|^2
+    lin = 0.5 * (L0 + quad - L1)               # <Au, I>
+    if not quad > 0:
+        return torch.zeros_like(u), L0
+    c0 = ((lin / quad) * u).contiguous()
+    Lw, _ = h.gradient_residual(c0, I, None, want_grad=False)
+    if Lw >= L0:
+        return torch.zeros_like(u), L0
+    return c0, Lw
+
+
+def iterations_to(h: tt.Handle, I, c0, L0: float, Lstar: float, target: float, max_iter: int):
+    """(iterations, evaluations, seconds) of L-BFGS from c0 until
+    (L - L*)/(L0 - L*) <= target."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    opt = tt.LBFGS(h, c0, I, None, m=10)
+    it, ev = 0, 1
+    while (opt.loss - Lstar) > target * (L0 - Lstar) and it < max_iter:
+        _, ne, st = opt.step()
+        it += 1
+        ev += ne
+        if st != tt.TT_OK:
+            break
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    opt.close()
+    return it, ev, dt
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=512)
+    ap.add_argument("--test", type=int, default=32)
+    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--target-iters", type=int, default=60, help="plain L-BFGS iterations of a training target")
+    ap.add_argument("--ref-iters", type=int, default=150, help="L-BFGS iterations defining L* of a test phantom")
+    ap.add_argument("--lr", type=float, default=1e-3)
+    args = ap.parse_args(argv)
+
+    # training: 64^3, l_max 4, 120 projections of 64x64 x 16 segments, seeds 100..
+    st_tr = synth.workload("ell64")
+    h_tr = tt.Handle(st_tr, "f32")
+    z_tr = torch.zeros(st_tr.volume_shape, dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    data = []
+    for s in range(args.train):
+        I, _ = phantom_data(h_tr, st_tr, 6, 100 + s)
+        _, g0 = h_tr.gradient_residual(z_tr, I, None)
+        cstar, _ = plain_solve(h_tr, I, args.target_iters)
+        data.append((g0, cstar, float(g0.pow(2).mean().sqrt()), float(cstar.pow(2).mean().sqrt())))
+        del I
+    t_data = time.perf_counter() - t0
+    net = tt.WarmStartNet(15, 15, seed=0)
+    t0 = time.perf_counter()
+    losses = []
+    for epoch in range(args.epochs):
+        order = np.random.default_rng(epoch).permutation(len(data))
+        ep = [net.train_step(data[i][0], data[i][1], data[i][2], args.lr, out_scale=data[i][3]) for i in order]
+        losses.append(float(np.mean(ep)))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del data
+
+    # test: 128^3, l_max 4, 240 projections of 128x128 x 16 segments, held-out seeds
+    st = synth.workload("ell128c16")
+    h32 = tt.Handle(st, "f32")
+    h16 = tt.Handle(st, "bf16")
+    z = torch.zeros(st.volume_shape, dtype=torch.float32, device="cuda")
+    rows = []
+    for s in range(args.test):
+        I, _ = phantom_data(h32, st, 6, 5000 + s)
+        L0, g0 = h32.gradient_residual(z, I, None)
+        _, Lstar = plain_solve(h32, I, args.ref_iters)
+        torch.cuda.synchronize()
+        t_ws = time.perf_counter()
+        c0, Lw = warm_start(net, h32, I, g0, L0)
+        torch.cuda.synchronize()
+        t_ws = time.perf_counter() - t_ws
+        zero = iterations_to(h32, I, z, L0, Lstar, 1e-3, args.ref_iters)
+        warm = iterations_to(h32, I, c0, L0, Lstar, 1e-3, args.ref_iters)
+        warm16 = iterations_to(h16, I, c0, L0, Lstar, 1e-3, args.ref_iters)
+        rows.append({"seed": 5000 + s, "L0": L0, "L_star": Lstar, "L_warm_over_L0": Lw / L0,
+                     "zero_f32": zero, "warm_f32": warm, "warm_bf16": warm16, "warm_start_s": t_ws})
+        del I, g0, c0
+
+    def agg(key, i):
+        return float(np.mean([r[key][i] for r in rows]))
+
+    out = {
+        "experiment": "learned warm start",
+        "train": {"workload": "64^3, l_max 4, 120 x 64x64 x 16, 6-ellipsoid phantoms, seeds 100..",
+                  "samples": args.train, "epochs": args.epochs, "target_iters": args.target_iters,
+                  "data_seconds": t_data, "train_seconds": t_train, "epoch_mean_loss": losses},
+        "test": {"workload": "128^3, l_max 4, 240 x 128x128 x 16, 6-ellipsoid phantoms, held-out seeds 5000..",
+                 "samples": args.test, "criterion": f"(L - L*)/(L0 - L*) <= 1e-3, L* after {args.ref_iters} iterations",
+                 "mean_L_warm_over_L0": float(np.mean([r["L_warm_over_L0"] for r in rows])),
+                 "zero_f32": {"iterations": agg("zero_f32", 0), "evals": agg("zero_f32", 1), "seconds": agg("zero_f32", 2)},
+                 "warm_f32": {"iterations": agg("warm_f32", 0), "evals": agg("warm_f32", 1), "seconds": agg("warm_f32", 2),
+                              "warm_start_seconds": float(np.mean([r["warm_start_s"] for r in rows]))},
+                 "warm_bf16": {"iterations": agg("warm_bf16", 0), "evals": agg("warm_bf16", 1),
+                               "seconds": agg("warm_bf16", 2)}},
+        "per_sample": rows,
+    }
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
