@@ -239,6 +239,34 @@ def time_to_loss(h, I, W, torch, tt, ref_iters: int, target: float = 1e-3, L0_Ls
             "L0": L0, "L_star": Lstar}
 
 
+def mitra_vs_lbfgs(h, I, W, torch, tt, ref_iters: int, target: float = 1e-3, max_iter: int = 3000):
+    """SIRT-weighted objective L_R(c) = sum R (A c - I)^2 (R from the data
+    weights W): wall time and iterations of the SIRT-preconditioned Nesterov
+    solver (tt_mitra_*, one evaluation per iteration, criterion on L_R at its
+    extrapolated point) and of L-BFGS on the same objective, until
+    (L_R - L_R*)/(L_R(0) - L_R*) <= target; L_R* = L-BFGS after ref_iters."""
+    R, _ = h.sirt_weights(W)
+    L0, Lstar = reference_loss(h, I, R, torch, tt, ref_iters)
+    lb = time_to_loss(h, I, R, torch, tt, ref_iters, target, L0_Lstar=(L0, Lstar))
+    z = torch.zeros(h.volume_shape, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m = tt.MITRA(h, z, I, W, eta=1.0, momentum=-1.0)
+    it, L = 0, L0
+    while (L - Lstar) > target * (L0 - Lstar) and it < max_iter:
+        L = m.step()
+        it += 1
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    m.close()
+    return {"objective": "sum R (A c - I)^2, R = W / (|A| 1), preconditioner 1 / (|A|^T 1)",
+            "criterion": f"(L_R - L_R*)/(L_R(0) - L_R*) <= {target:g}",
+            "mitra_nesterov": {"seconds": dt, "iterations": it, "evals": it,
+                               "ms_per_iteration": 1e3 * dt / max(it, 1),
+                               "reached": bool((L - Lstar) <= target * (L0 - Lstar))},
+            "lbfgs": {k: lb[k] for k in ("seconds", "iterations", "evals", "reached")}}
+
+
 def measure_forms(torch, tt, synth, flush, steps: int = 20):
     """ms per gradient evaluation of the FP32, bfloat16- and float16-storage
     forms on the 64^3 (l_max 4) and 128^3 (l_max 8, 240 x 128^2 x 8) workloads;
@@ -395,6 +423,7 @@ def run_ours(args):
         hb = tt.Handle(st, "bf16")
         out["time_to_loss"]["bf16"] = time_to_loss(hb, I, W, torch, tt, args.ttl_ref_iters, L0_Lstar=ref)
         hb.close()
+        out["time_to_loss"]["sirt_weighted"] = mitra_vs_lbfgs(h, I, W, torch, tt, args.ttl_ref_iters)
     if not args.no_forms:
         out["forms"] = measure_forms(torch, tt, synth, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

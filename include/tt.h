@@ -97,6 +97,7 @@ typedef struct {
 
 typedef struct tt_handle tt_handle;
 typedef struct tt_lbfgs tt_lbfgs;
+typedef struct tt_mitra tt_mitra;
 
 /* Number of even-order real SH coefficients K for a band limit. */
 int tt_num_coeffs(int ell_max);
@@ -204,6 +205,46 @@ tt_status tt_lbfgs_step(tt_handle *h, tt_lbfgs *st, void *c_out_dev, double *los
 tt_status tt_lbfgs_get(tt_handle *h, tt_lbfgs *st, void *c_dev, void *g_dev, double *loss_host);
 /* Frees the state; valid before or after tt_destroy of its handle. */
 tt_status tt_lbfgs_destroy(tt_lbfgs *st);
+
+/* ---- SIRT-preconditioned solver (Section "Standard reconstruction
+ * pipelines": SIRT as preconditioned gradient descent on weighted least
+ * squares, the same weights applied to the full model A = B_s (x) P_s, and
+ * Nesterov momentum).  The paper gives no formulas; the weights are built
+ * from |A| = |B_s| (x) P_s (the John-transform coefficients are >= 0):
+ *   rho[s][j][k][c] = (sum_i |B_s[c][i]|) (P_s 1)[j][k]        row sums of |A|
+ *   kappa[v][i]     = sum_s (sum_c |B_s[c][i]|) (P_s^T 1)[v]  column sums
+ *   R = W / rho (0 on rays whose length in the volume is <= 1e-6 a)
+ *   D = 1 / kappa (0 where kappa <= 1e-6 a / (2 sqrt(pi)))
+ * With 0 <= W <= 1, ||R^1/2 A D^1/2||_2 <= 1 (Cauchy-Schwarz), so the
+ * iteration below is stable for 0 < eta < 2.
+ *
+ * tt_sirt_weights: R_dev [S][nj][nk][C] and D_dev [nx][ny][nz][K] (caller
+ * allocated, 16-byte aligned, handle precision's API type) from the
+ * optional data weights W_dev (NULL = 1).  Runs the projector kernels on a
+ * unit volume, so it overwrites the handle's internal buffers (not the
+ * caller's).  Asynchronous on the handle's stream. */
+tt_status tt_sirt_weights(tt_handle *h, const float *W_dev, float *R_dev, float *D_dev);
+tt_status tt_sirt_weights_f64(tt_handle *h, const double *W_dev, double *R_dev, double *D_dev);
+/* Solver state for minimising L_R(c) = sum R (A c - I)^2 by
+ *   y_t = x_t + mu_t (x_t - x_{t-1}),   x_{t+1} = y_t - (eta/2) D grad L_R(y_t)
+ * (x_1 = x_0 = c0; eta = 1, momentum = 0 is the classical SIRT update
+ * x + D A^T R (I - A x)).  momentum < 0 selects the Nesterov schedule
+ * mu_t = (t-1)/(t+2); otherwise mu_t = momentum.  Needs 0 < eta < 2 and
+ * momentum < 1 (else TT_INVALID_ARG).  c0_dev and W_dev are copied (the
+ * weights into R); I_dev [S][nj][nk][C] must stay valid for the state's
+ * life.  Pointers are device pointers of the handle's API type. */
+tt_status tt_mitra_create(tt_handle *h, const void *c0_dev, const void *I_dev, const void *W_dev,
+                          double eta, double momentum, tt_mitra **out);
+/* One iteration: one gradient-residual evaluation at y_t and one update
+ * kernel.  loss_host (may be NULL) receives L_R(y_t) and synchronises the
+ * stream; with NULL the call only enqueues work (no host synchronisation). */
+tt_status tt_mitra_step(tt_mitra *m, double *loss_host);
+/* Copies the iterate x (c_dev, [nx][ny][nz][K]), the data weights R
+ * (R_dev) and the preconditioner D (D_dev); any may be NULL.  *iterations
+ * (may be NULL) = iterations taken. */
+tt_status tt_mitra_get(tt_mitra *m, void *c_dev, void *R_dev, void *D_dev, int *iterations);
+/* Frees the state; valid before or after tt_destroy of its handle. */
+tt_status tt_mitra_destroy(tt_mitra *m);
 
 /* Learned warm start: a 3-D convolutional network (4 layers of 3x3x3
  * convolutions, k_in -> 32 -> 32 -> 32 -> k_out channels, ReLU between

@@ -85,6 +85,12 @@ SIGNATURES = {
     "tt_lbfgs_step": (ctypes.c_int, [_P, _P, _P, _D, ctypes.POINTER(ctypes.c_int)]),
     "tt_lbfgs_get": (ctypes.c_int, [_P, _P, _P, _P, _D]),
     "tt_lbfgs_destroy": (ctypes.c_int, [_P]),
+    "tt_sirt_weights": (ctypes.c_int, [_P, _P, _P, _P]),
+    "tt_sirt_weights_f64": (ctypes.c_int, [_P, _P, _P, _P]),
+    "tt_mitra_create": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_P)]),
+    "tt_mitra_step": (ctypes.c_int, [_P, _D]),
+    "tt_mitra_get": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
+    "tt_mitra_destroy": (ctypes.c_int, [_P]),
     "tt_wsnet_num_weights": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "tt_wsnet_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(_P)]),
     "tt_wsnet_destroy": (ctypes.c_int, [_P]),
@@ -288,6 +294,17 @@ class Handle:
                   None if g is None else ctypes.c_void_p(g.data_ptr()), ctypes.byref(v)), "tt_tv_huber")
         return v.value, g
 
+    def sirt_weights(self, W=None):
+        """(R, D): SIRT data weights [S, nj, nk, C] and preconditioner [nx, ny, nz, K]
+        (inverse row / column sums of |A|; see tt_sirt_weights in include/tt.h)."""
+        self._sync_stream()
+        R = torch.empty(self.data_shape, dtype=self.dtype, device="cuda")
+        D = torch.empty(self.volume_shape, dtype=self.dtype, device="cuda")
+        fn = getattr(self.lib, "tt_sirt_weights" + self._sfx)
+        _check(fn(self._h, None if W is None else _dptr(W, self.dtype, self.data_shape, "W"),
+                  ctypes.c_void_p(R.data_ptr()), ctypes.c_void_p(D.data_ptr())), "tt_sirt_weights")
+        return R, D
+
     # ------------------------------------------------------------ profiling
     def profile(self, enable: bool = True):
         _check(self.lib.tt_profile_enable(self._h, int(enable)), "tt_profile_enable")
@@ -346,6 +363,52 @@ class LBFGS:
     def close(self):
         if getattr(self, "_st", None):
             self.h.lib.tt_lbfgs_destroy(self._st)
+            self._st = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MITRA:
+    """SIRT-preconditioned gradient descent with Nesterov momentum (tt_mitra_*)."""
+
+    def __init__(self, handle: Handle, c0: torch.Tensor, I: torch.Tensor, W: torch.Tensor | None = None,
+                 eta: float = 1.0, momentum: float = -1.0):
+        self.h = handle
+        handle._sync_stream()
+        self._keep = I
+        st = _P()
+        dt, vs, ds = handle.dtype, handle.volume_shape, handle.data_shape
+        _check(handle.lib.tt_mitra_create(handle._h, _dptr(c0, dt, vs, "c0"), _dptr(I, dt, ds, "I"),
+                                          None if W is None else _dptr(W, dt, ds, "W"), float(eta),
+                                          float(momentum), ctypes.byref(st)), "tt_mitra_create")
+        self._st = st
+
+    def step(self, want_loss: bool = True):
+        """One iteration; returns L_R at the extrapolated point (None if not wanted:
+        then nothing synchronises with the host)."""
+        self.h._sync_stream()
+        loss = ctypes.c_double(0.0)
+        _check(self.h.lib.tt_mitra_step(self._st, ctypes.byref(loss) if want_loss else None), "tt_mitra_step")
+        return loss.value if want_loss else None
+
+    def get(self):
+        """(x, R, D, iterations)."""
+        self.h._sync_stream()
+        x = torch.empty(self.h.volume_shape, dtype=self.h.dtype, device="cuda")
+        R = torch.empty(self.h.data_shape, dtype=self.h.dtype, device="cuda")
+        D = torch.empty_like(x)
+        it = ctypes.c_int(0)
+        _check(self.h.lib.tt_mitra_get(self._st, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(R.data_ptr()),
+                                       ctypes.c_void_p(D.data_ptr()), ctypes.byref(it)), "tt_mitra_get")
+        return x, R, D, it.value
+
+    def close(self):
+        if getattr(self, "_st", None):
+            self.h.lib.tt_mitra_destroy(self._st)
             self._st = None
 
     def __del__(self):
