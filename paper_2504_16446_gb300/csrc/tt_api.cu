@@ -328,8 +328,10 @@ tt_status tt_grad_enqueue(tt_handle *h, const T *c, const T *I, const T *W, T *g
     return with_storage<T>(h, [&]<typename S>() -> tt_status {
         TT_CUDA((launch_pack<T, S>(h, c)), "pack");
         TT_CUDA((launch_forward<T, S>(h, nullptr, I, W, true)), "forward");
-        TT_CUDA(launch_reduce(h, h->partials, h->n_fwd_ctas, h->loss_dev, nullptr, 1.0), "loss reduce");
-        if (g) TT_CUDA((launch_adjoint<T, S>(h, g)), "adjoint");
+        // the adjoint's first CTA reduces the loss partials; without a
+        // gradient a one-CTA reduction does
+        if (g) TT_CUDA((launch_adjoint<T, S>(h, g, true)), "adjoint");
+        else TT_CUDA(launch_reduce(h, h->partials, h->n_fwd_ctas, h->loss_dev, nullptr, 1.0), "loss reduce");
         return TT_OK;
     });
 }

@@ -25,6 +25,13 @@ __host__ __device__ constexpr int padded_k(int K) {
     return ((K + 4 * lane_group(K) - 1) / (4 * lane_group(K))) * (4 * lane_group(K));
 }
 __host__ __device__ constexpr int num_coeffs(int L) { return (L + 1) * (L + 2) / 2; }
+// Voxels a lane group of the adjoint owns: all LG while a lane's accumulators
+// (V * KP / LG) fit in 16 registers' worth of channels, else as many as keep
+// them within 24 (one for the largest K).
+__host__ __device__ constexpr int adjoint_voxels(int KP, int LG)
+{
+    return KP / LG <= 4 ? LG : ((24 / (KP / LG)) < 1 ? 1 : ((24 / (KP / LG)) > LG ? LG : 24 / (KP / LG)));
+}
 
 // Per-projection constants of the Joseph discretisation, in voxel-index
 // units (computed on the host in FP64 from Eq. real_space_geom).
@@ -149,8 +156,12 @@ template <typename T, typename S>
 cudaError_t launch_backcontract(tt_handle *h, const T *R);
 // g [nvox][K] (unpadded) = exact-transpose gather of G; S above one
 // parameter block runs several launches accumulating in h->gpad.
+// With reduce_loss the first launch also sums the forward's per-CTA loss
+// partials (h->partials, h->n_fwd_ctas) into h->loss_dev[0], in the order of
+// launch_reduce, so that the gradient evaluation needs no separate
+// reduction launch.
 template <typename T, typename S>
-cudaError_t launch_adjoint(tt_handle *h, T *g);
+cudaError_t launch_adjoint(tt_handle *h, T *g, bool reduce_loss = false);
 cudaError_t launch_reduce(tt_handle *h, const double *partials, long long n, double *out,
                           const double *add, double mul);
 cudaError_t launch_basis(tt_handle *h, const double *nodes, const double *weights);

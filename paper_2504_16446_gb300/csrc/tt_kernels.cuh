@@ -25,6 +25,15 @@ namespace tt {
 
 // ----------------------------------------------------------- vector helpers
 
+// (a0, a1) += w * (x0, x1) as one paired FP32 FMA (sm_100+): each lane is
+// rounded exactly like fmaf, at half the issue slots.
+__device__ __forceinline__ void fma2(float &a0, float &a1, float w, float x0, float x1)
+{
+    const float2 r = __ffma2_rn(make_float2(w, w), make_float2(x0, x1), make_float2(a0, a1));
+    a0 = r.x;
+    a1 = r.y;
+}
+
 template <typename T, int CPL>
 __device__ __forceinline__ void fma_row(T (&acc)[CPL], T w, const T *__restrict__ p)
 {
@@ -32,11 +41,9 @@ __device__ __forceinline__ void fma_row(T (&acc)[CPL], T w, const T *__restrict_
         static_assert(CPL % 4 == 0, "float rows are read as float4");
 #pragma unroll
         for (int t = 0; t < CPL / 4; ++t) {
-            float4 x = __ldg(reinterpret_cast<const float4 *>(p) + t);
-            acc[4 * t + 0] = fmaf(w, x.x, acc[4 * t + 0]);
-            acc[4 * t + 1] = fmaf(w, x.y, acc[4 * t + 1]);
-            acc[4 * t + 2] = fmaf(w, x.z, acc[4 * t + 2]);
-            acc[4 * t + 3] = fmaf(w, x.w, acc[4 * t + 3]);
+            const float4 x = __ldg(reinterpret_cast<const float4 *>(p) + t);
+            fma2(acc[4 * t + 0], acc[4 * t + 1], w, x.x, x.y);
+            fma2(acc[4 * t + 2], acc[4 * t + 3], w, x.z, x.w);
         }
     } else {
         static_assert(CPL % 2 == 0, "double rows are read as double2");
@@ -102,8 +109,7 @@ __device__ __forceinline__ void fma_row_s(T (&acc)[CPL], T w, const S *__restric
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const float2 f = unpack2(uu[k], (S *)nullptr);
-                    acc[8 * t + 2 * k] = fmaf(w, f.x, acc[8 * t + 2 * k]);
-                    acc[8 * t + 2 * k + 1] = fmaf(w, f.y, acc[8 * t + 2 * k + 1]);
+                    fma2(acc[8 * t + 2 * k], acc[8 * t + 2 * k + 1], w, f.x, f.y);
                 }
             }
         } else {
@@ -111,10 +117,8 @@ __device__ __forceinline__ void fma_row_s(T (&acc)[CPL], T w, const S *__restric
             for (int t = 0; t < CPL / 4; ++t) {
                 const uint2 u = __ldg(reinterpret_cast<const uint2 *>(p) + t);
                 const float2 f0 = unpack2(u.x, (S *)nullptr), f1 = unpack2(u.y, (S *)nullptr);
-                acc[4 * t] = fmaf(w, f0.x, acc[4 * t]);
-                acc[4 * t + 1] = fmaf(w, f0.y, acc[4 * t + 1]);
-                acc[4 * t + 2] = fmaf(w, f1.x, acc[4 * t + 2]);
-                acc[4 * t + 3] = fmaf(w, f1.y, acc[4 * t + 3]);
+                fma2(acc[4 * t], acc[4 * t + 1], w, f0.x, f0.y);
+                fma2(acc[4 * t + 2], acc[4 * t + 3], w, f1.x, f1.y);
             }
         }
     }
@@ -155,6 +159,26 @@ __device__ __forceinline__ double block_sum(double v, double *red)
         t = warp_sum(t);
     }
     return t;
+}
+
+// Sum of p[0..n) in a fixed order, for a block of kThreads threads: thread t
+// keeps eight running sums over t + kThreads i (i = 0, 1, ... taken round
+// robin), adds them pairwise, then block_sum.  The eight independent load
+// chains keep a single-CTA reduction short.  The result is valid on thread 0.
+__device__ __forceinline__ double sum_fixed_order(const double *__restrict__ p, long long n, double *red)
+{
+    constexpr long long B = kThreads;
+    double v8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    long long t = threadIdx.x;
+    for (; t + 7 * B < n; t += 8 * B) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v8[i] += __ldg(p + t + i * B);
+    }
+#pragma unroll
+    for (int i = 0; i < 7; ++i)
+        if (t + i * B < n) v8[i] += __ldg(p + t + i * B);
+    const double v = ((v8[0] + v8[1]) + (v8[2] + v8[3])) + ((v8[4] + v8[5]) + (v8[6] + v8[7]));
+    return block_sum(v, red);
 }
 
 // Range of planes p in [0, Nm-1] on which coordinate w(p) = w0 + p*dw lies
@@ -416,21 +440,24 @@ __device__ __forceinline__ int sel3(int x, int y, int z, int axis)
 // floor(kc - hk) + 1); the window shape is uniform per projection, so the
 // candidate loop is unrolled per shape.
 //
-// Work split: a lane group of LG lanes owns LG voxels (consecutive in z).
-// Lane q does the candidate geometry for voxel q only, then the group
-// broadcasts each candidate's (row, weight) with shuffles and every lane
-// accumulates its own channel chunk q of that row for all LG voxels.  The
-// geometry is thus computed once per voxel while a G row is still read as
-// one contiguous KP-float segment by the LG lanes together.  Per-projection
-// constants travel in the kernel's parameter space.
-template <typename T, typename S, int CPL, int KP, int LG, int NJ, int NK>
-__device__ __forceinline__ void adj_window(T (&acc)[LG][CPL], const S *__restrict__ Gq, int nk, int r0, T du0,
+// Work split: a lane group of LG lanes owns V <= LG voxels (consecutive in
+// z).  Lane q does the candidate geometry for voxel q % V only, then the
+// group exchanges each candidate's (row, weight) -- through shared memory
+// for FP32 (one 16-byte read gives a candidate's weights for all sources;
+// shuffles would take a load-store-unit wavefront per source), with
+// shuffles otherwise -- and every lane accumulates its own channel chunk q
+// of that row for all V voxels (with V == 1 every lane already holds them).
+// The geometry is thus computed once per voxel while a G row is still read
+// as one contiguous KP-float segment by the LG lanes together.
+// Per-projection constants travel in the kernel's parameter space.
+template <typename T, typename S, int CPL, int KP, int LG, int V, int NJ, int NK>
+__device__ __forceinline__ void adj_window(T (&acc)[V][CPL], const S *__restrict__ Gq, int nk, int r0, T du0,
                                            T dv0, const AdjProj<T> &c, unsigned jmask, unsigned kmask)
 {
     // window origin row of every source voxel of the group (one shuffle each)
-    int r0s[LG];
+    int r0s[V];
 #pragma unroll
-    for (int src = 0; src < LG; ++src) r0s[src] = (LG == 1) ? r0 : __shfl_sync(0xffffffffu, r0, src, LG);
+    for (int src = 0; src < V; ++src) r0s[src] = (LG == 1 || V == 1) ? r0 : __shfl_sync(0xffffffffu, r0, src, LG);
 #pragma unroll
     for (int a = 0; a < NJ; ++a) {
 #pragma unroll
@@ -443,16 +470,57 @@ __device__ __forceinline__ void adj_window(T (&acc)[LG][CPL], const S *__restric
             const T w = hit ? tu * tv : T(0);
             const int off = a * nk + b;
 #pragma unroll
-            for (int src = 0; src < LG; ++src) {
-                const T ws = (LG == 1) ? w : __shfl_sync(0xffffffffu, w, src, LG);
+            for (int src = 0; src < V; ++src) {
+                const T ws = (LG == 1 || V == 1) ? w : __shfl_sync(0xffffffffu, w, src, LG);
                 if (ws != T(0)) fma_row_s<T, S, CPL>(acc[src], ws, Gq + (long long)(r0s[src] + off) * KP);
             }
         }
     }
 }
 
-template <typename T, typename S, int CPL, int KP, int LG>
-__device__ __forceinline__ void adj_window_any(T (&acc)[LG][CPL], const S *__restrict__ Gq, int nj, int nk, int j0,
+// Same as adj_window, but the group exchanges the candidates' weights and
+// window rows through shared memory: lane q publishes its voxel's weights
+// (one store per candidate), then every lane reads the V sources' weights of
+// a candidate with one 16-byte load instead of V shuffles.
+template <typename S, int CPL, int KP, int LG, int V, int NJ, int NK>
+__device__ __forceinline__ void adj_window_sm(float (&acc)[V][CPL], const S *__restrict__ Gq, int nk, int r0,
+                                              float du0, float dv0, const AdjProj<float> &c, unsigned jmask,
+                                              unsigned kmask, float *__restrict__ wb, int *__restrict__ rb, int q)
+{
+    static_assert(V >= 2 && V <= 4 && NJ * NK <= 9, "weight exchange holds 4 sources x 9 candidates");
+    if (q < V) rb[q] = r0;
+#pragma unroll
+    for (int a = 0; a < NJ; ++a) {
+#pragma unroll
+        for (int b = 0; b < NK; ++b) {
+            const float du = du0 + (float)a * c.uj + (float)b * c.uk;
+            const float dv = dv0 + (float)a * c.vj + (float)b * c.vk;
+            const float tu = 1.f - fabsf(du);
+            const float tv = c.step - c.step * fabsf(dv);
+            const bool hit = ((jmask >> a) & (kmask >> b) & 1u) && tu > 0.f && tv > 0.f;
+            if (q < V) wb[(a * NK + b) * 4 + q] = hit ? tu * tv : 0.f;
+        }
+    }
+    __syncwarp();
+    const int4 r4 = *reinterpret_cast<const int4 *>(rb);
+    const int rs[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+    for (int a = 0; a < NJ; ++a) {
+#pragma unroll
+        for (int b = 0; b < NK; ++b) {
+            const float4 w4 = *reinterpret_cast<const float4 *>(wb + (a * NK + b) * 4);
+            const float ws[4] = {w4.x, w4.y, w4.z, w4.w};
+            const int off = a * nk + b;
+#pragma unroll
+            for (int src = 0; src < V; ++src)
+                if (ws[src] != 0.f) fma_row_s<float, S, CPL>(acc[src], ws[src], Gq + (long long)(rs[src] + off) * KP);
+        }
+    }
+    __syncwarp();
+}
+
+template <typename T, typename S, int CPL, int KP, int LG, int V>
+__device__ __forceinline__ void adj_window_any(T (&acc)[V][CPL], const S *__restrict__ Gq, int nj, int nk, int j0,
                                             int k0, T du0, T dv0, const AdjProj<T> &c, bool valid)
 {
     for (int a = 0; a < c.nwj; ++a) {
@@ -466,7 +534,7 @@ __device__ __forceinline__ void adj_window_any(T (&acc)[LG][CPL], const S *__res
             const T w = hit ? tu * tv : T(0);
             const int row = (j0 + a) * nk + (k0 + b);
 #pragma unroll
-            for (int src = 0; src < LG; ++src) {
+            for (int src = 0; src < V; ++src) {
                 const T ws = (LG == 1) ? w : __shfl_sync(0xffffffffu, w, src, LG);
                 const int rs = (LG == 1) ? row : __shfl_sync(0xffffffffu, row, src, LG);
                 if (ws != T(0)) fma_row_s<T, S, CPL>(acc[src], ws, Gq + (long long)rs * KP);
@@ -475,17 +543,30 @@ __device__ __forceinline__ void adj_window_any(T (&acc)[LG][CPL], const S *__res
     }
 }
 
-template <typename T, typename S, int KP, int LG>
-__global__ void __launch_bounds__(kThreads, 3)
+// Four resident blocks (64 registers) pay off while a lane's accumulators are
+// 16 floats; larger K keeps three.
+template <typename T, typename S, int KP, int LG, int V>
+__global__ void __launch_bounds__(kThreads, (KP <= 16 ? 4 : 3))
 k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const S *__restrict__ G, int nj, int nk, int nx,
-          int ny, int nz, int ty, int tz, T *__restrict__ gpad, int accumulate, T *__restrict__ gout, int K)
+          int ny, int nz, int ty, int tz, T *__restrict__ gpad, int accumulate, T *__restrict__ gout, int K,
+          const double *__restrict__ loss_partials, long long n_partials, double *__restrict__ loss_out)
 {
+    // CTA 0 first sums the forward's loss partials (written by the previous
+    // launch on this stream, so visible here without fences).
+    if (loss_out && blockIdx.x == 0) {
+        __shared__ double lred[32];
+        const double v = sum_fixed_order(loss_partials, n_partials, lred);
+        if (threadIdx.x == 0) loss_out[0] = v;
+    }
     constexpr int CPL = KP / LG;
-    // A warp's 32/LG lane groups take consecutive z, and lane q of a group
-    // owns the voxel (32/LG) * q further along z, so that the rows the warp
-    // reads for one broadcast source are rays of neighbouring voxels.
+    // A warp's 32/LG lane groups take consecutive z; a group owns V voxels,
+    // source v being (32/LG) * v further along z, so that the rows the warp
+    // reads for one broadcast source are rays of neighbouring voxels.  Lane
+    // q computes the candidate geometry of voxel q % V (V <= LG; with V < LG
+    // lanes repeat a voxel's geometry so that the accumulators, V * CPL per
+    // lane, stay in registers for large K).
     constexpr int GPW = 32 / LG;                   // lane groups per warp
-    constexpr int BZ = 32, BY = 4, BX = (kThreads / 32) / BY;
+    constexpr int BZ = GPW * V, BY = 4, BX = (kThreads / 32) / BY;
 
     const int b = blockIdx.x;
     const int bz = b % tz, by = (b / tz) % ty, bx = b / (tz * ty);
@@ -493,16 +574,21 @@ k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const S *__restrict__ 
     const int gw = lane / LG, q = lane % LG;
     const int x = bx * BX + warp / BY, y = by * BY + warp % BY;
     const int z0 = bz * BZ + gw;                   // voxel of source v is z0 + GPW * v
-    const int z = z0 + GPW * q;
+    const int z = z0 + GPW * (q % V);
     const bool valid = (x < nx) && (y < ny) && (z < nz);
     const T fx = (T)x, fy = (T)y, fz = (T)z;
 
-    T acc[LG][CPL];
+    T acc[V][CPL];
 #pragma unroll
-    for (int v = 0; v < LG; ++v)
+    for (int v = 0; v < V; ++v)
 #pragma unroll
         for (int i = 0; i < CPL; ++i) acc[v][i] = T(0);
     const size_t gstride = (size_t)nj * nk * KP;
+    constexpr bool kSmem = std::is_same<T, float>::value && V >= 2;
+    __shared__ __align__(16) float s_w[kSmem ? (kThreads / LG) * 36 : 1];
+    __shared__ __align__(16) int s_r[kSmem ? (kThreads / LG) * 4 : 1];
+    float *wb = s_w + (kSmem ? (threadIdx.x / LG) * 36 : 0);
+    int *rb = s_r + (kSmem ? (threadIdx.x / LG) * 4 : 0);
 
     // Warps whose voxels all lie outside the volume skip the loop as a whole.
     const bool group_live = (x < nx) && (y < ny) && (bz * BZ < nz);
@@ -527,22 +613,22 @@ k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const S *__restrict__ 
             if (!valid) { jm = 0; km = 0; }
             const S *Gq = G + (size_t)si * gstride + q * CPL;
             switch (c.shape) {
-            case 0x11: adj_window<T, S, CPL, KP, LG, 1, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            case 0x12: adj_window<T, S, CPL, KP, LG, 1, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            case 0x13: adj_window<T, S, CPL, KP, LG, 1, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            case 0x21: adj_window<T, S, CPL, KP, LG, 2, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            case 0x22: adj_window<T, S, CPL, KP, LG, 2, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            case 0x23: adj_window<T, S, CPL, KP, LG, 2, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            case 0x31: adj_window<T, S, CPL, KP, LG, 3, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            case 0x32: adj_window<T, S, CPL, KP, LG, 3, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            case 0x33: adj_window<T, S, CPL, KP, LG, 3, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
-            default: adj_window_any<T, S, CPL, KP, LG>(acc, Gq, nj, nk, j0, k0, du0, dv0, c, valid); break;
+            case 0x11: if constexpr (kSmem) adj_window_sm<S, CPL, KP, LG, V, 1, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km, wb, rb, q); else adj_window<T, S, CPL, KP, LG, V, 1, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x12: if constexpr (kSmem) adj_window_sm<S, CPL, KP, LG, V, 1, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km, wb, rb, q); else adj_window<T, S, CPL, KP, LG, V, 1, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x13: if constexpr (kSmem) adj_window_sm<S, CPL, KP, LG, V, 1, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km, wb, rb, q); else adj_window<T, S, CPL, KP, LG, V, 1, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x21: if constexpr (kSmem) adj_window_sm<S, CPL, KP, LG, V, 2, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km, wb, rb, q); else adj_window<T, S, CPL, KP, LG, V, 2, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x22: if constexpr (kSmem) adj_window_sm<S, CPL, KP, LG, V, 2, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km, wb, rb, q); else adj_window<T, S, CPL, KP, LG, V, 2, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x23: if constexpr (kSmem) adj_window_sm<S, CPL, KP, LG, V, 2, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km, wb, rb, q); else adj_window<T, S, CPL, KP, LG, V, 2, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x31: if constexpr (kSmem) adj_window_sm<S, CPL, KP, LG, V, 3, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km, wb, rb, q); else adj_window<T, S, CPL, KP, LG, V, 3, 1>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x32: if constexpr (kSmem) adj_window_sm<S, CPL, KP, LG, V, 3, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km, wb, rb, q); else adj_window<T, S, CPL, KP, LG, V, 3, 2>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            case 0x33: if constexpr (kSmem) adj_window_sm<S, CPL, KP, LG, V, 3, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km, wb, rb, q); else adj_window<T, S, CPL, KP, LG, V, 3, 3>(acc, Gq, nk, r0, du0, dv0, c, jm, km); break;
+            default: adj_window_any<T, S, CPL, KP, LG, V>(acc, Gq, nj, nk, j0, k0, du0, dv0, c, valid); break;
             }
         }
     }
-    // lane q writes channel chunk q of the group's LG voxels
+    // lane q writes channel chunk q of the group's V voxels
 #pragma unroll
-    for (int v = 0; v < LG; ++v) {
+    for (int v = 0; v < V; ++v) {
         const int zv = z0 + GPW * v;
         if (!(x < nx && y < ny && zv < nz)) continue;
         const long long vox = ((long long)x * ny + y) * nz + zv;
@@ -612,10 +698,10 @@ cudaError_t launch_backcontract_L(tt_handle *h, const T *R)
 }
 
 template <typename T, typename S, int L>
-cudaError_t launch_adjoint_L(tt_handle *h, T *g)
+cudaError_t launch_adjoint_L(tt_handle *h, T *g, bool reduce_loss)
 {
-    constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K);
-    constexpr int BZ = 32, BY = 4, BX = (kThreads / 32) / BY;
+    constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K), V = adjoint_voxels(KP, LG);
+    constexpr int BZ = (32 / LG) * V, BY = 4, BX = (kThreads / 32) / BY;
     const int tx = (h->N[0] + BX - 1) / BX, ty = (h->N[1] + BY - 1) / BY, tz = (h->N[2] + BZ - 1) / BZ;
     const std::vector<AdjParams<T>> &chunks = adj_params<T>(h);
     const S *G = (const S *)h->G;
@@ -627,9 +713,10 @@ cudaError_t launch_adjoint_L(tt_handle *h, T *g)
         const bool last = ci == nchunk - 1;
         cudaEvent_t ev;
         prof_begin(h, TT_KSLOT_ADJOINT, &ev);
-        k_adjoint<T, S, KP, LG><<<(unsigned)(tx * ty * tz), kThreads, 0, h->stream>>>(
+        k_adjoint<T, S, KP, LG, V><<<(unsigned)(tx * ty * tz), kThreads, 0, h->stream>>>(
             chunks[ci], ns, G + (size_t)s0 * h->nj * h->nk * KP, h->nj, h->nk, h->N[0], h->N[1], h->N[2], ty, tz,
-            (T *)h->gpad, ci > 0 ? 1 : 0, last ? g : nullptr, h->K);
+            (T *)h->gpad, ci > 0 ? 1 : 0, last ? g : nullptr, h->K, h->partials, h->n_fwd_ctas,
+            (reduce_loss && ci == 0) ? h->loss_dev : nullptr);
         e = cudaGetLastError();
         prof_end(h, TT_KSLOT_ADJOINT, ev);
     }
@@ -667,16 +754,16 @@ cudaError_t launch_adjoint_L(tt_handle *h, T *g)
         }                                                                                      \
     }                                                                                          \
     template <>                                                                                \
-    cudaError_t launch_adjoint<T, S>(tt_handle * h, T * g)                                     \
+    cudaError_t launch_adjoint<T, S>(tt_handle * h, T * g, bool rl)                            \
     {                                                                                          \
         switch (h->L) {                                                                        \
-        case 0: return launch_adjoint_L<T, S, 0>(h, g);                                        \
-        case 2: return launch_adjoint_L<T, S, 2>(h, g);                                        \
-        case 4: return launch_adjoint_L<T, S, 4>(h, g);                                        \
-        case 6: return launch_adjoint_L<T, S, 6>(h, g);                                        \
-        case 8: return launch_adjoint_L<T, S, 8>(h, g);                                        \
-        case 10: return launch_adjoint_L<T, S, 10>(h, g);                                      \
-        case 12: return launch_adjoint_L<T, S, 12>(h, g);                                      \
+        case 0: return launch_adjoint_L<T, S, 0>(h, g, rl);                                    \
+        case 2: return launch_adjoint_L<T, S, 2>(h, g, rl);                                    \
+        case 4: return launch_adjoint_L<T, S, 4>(h, g, rl);                                    \
+        case 6: return launch_adjoint_L<T, S, 6>(h, g, rl);                                    \
+        case 8: return launch_adjoint_L<T, S, 8>(h, g, rl);                                    \
+        case 10: return launch_adjoint_L<T, S, 10>(h, g, rl);                                  \
+        case 12: return launch_adjoint_L<T, S, 12>(h, g, rl);                                  \
         default: return cudaErrorInvalidValue;                                                 \
         }                                                                                      \
     }

@@ -9,25 +9,39 @@ namespace tt {
 
 // Interior of the padded volume: cpad[x+2][y+2][z+2][i] = c[x][y][z][i] for
 // i < K, 0 for K <= i < KP (the two-voxel border is zeroed once at creation).
-template <typename T, typename S>
-__device__ __forceinline__ S to_storage(T x)
+// One thread per 4-channel chunk of a voxel: consecutive threads read
+// consecutive chunks of c and write consecutive 16-byte (8-byte for 2-byte
+// storage) pieces of cpad rows.  Index arithmetic is 32-bit (tt_create caps
+// the volume at 2^24 voxels).
+template <typename S>
+__device__ __forceinline__ void store4(S *p, float a, float b, float c, float d)
 {
-    if constexpr (std::is_same<S, __nv_bfloat16>::value) return __float2bfloat16_rn(x);
-    else if constexpr (std::is_same<S, __half>::value) return __float2half_rn(x);
-    else return x;
+    if constexpr (std::is_same<S, float>::value) {
+        *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+    } else {
+        *reinterpret_cast<uint2 *>(p) = make_uint2(pack2(a, b, (S *)nullptr), pack2(c, d, (S *)nullptr));
+    }
 }
 
 template <typename T, typename S>
 __global__ void k_pack(const T *__restrict__ c, S *__restrict__ cpad, int nx, int ny, int nz, int K, int KP)
 {
-    const long long n = (long long)nx * ny * nz * KP;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long v = t / KP;
-        const int i = (int)(t - v * KP);
-        const int z = (int)(v % nz), y = (int)((v / nz) % ny), x = (int)(v / ((long long)nz * ny));
-        const long long o = (((long long)(x + 2) * (ny + 4) + (y + 2)) * (nz + 4) + (z + 2)) * KP + i;
-        cpad[o] = to_storage<T, S>(i < K ? __ldg(c + v * K + i) : T(0));
+    const int QP = KP / 4;
+    const int n = nx * ny * nz * QP;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int v = t / QP, i0 = 4 * (t - v * QP);
+        const int z = v % nz, xy = v / nz, y = xy % ny, x = xy / ny;
+        const T *src = c + (long long)v * K;
+        T val[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) val[i] = i0 + i < K ? __ldg(src + i0 + i) : T(0);
+        S *dst = cpad + (((long long)(x + 2) * (ny + 4) + (y + 2)) * (nz + 4) + (z + 2)) * KP + i0;
+        if constexpr (std::is_same<T, double>::value) {
+            reinterpret_cast<double2 *>(dst)[0] = make_double2(val[0], val[1]);
+            reinterpret_cast<double2 *>(dst)[1] = make_double2(val[2], val[3]);
+        } else {
+            store4<S>(dst, val[0], val[1], val[2], val[3]);
+        }
     }
 }
 
@@ -56,8 +70,8 @@ cudaError_t launch_pack(tt_handle *h, const T *c)
 {
     cudaEvent_t ev;
     prof_begin(h, TT_KSLOT_PACK, &ev);
-    k_pack<T, S><<<grid_for(h->nvox() * h->KP), 256, 0, h->stream>>>(c, (S *)h->cpad, h->N[0], h->N[1], h->N[2],
-                                                                   h->K, h->KP);
+    k_pack<T, S><<<grid_for(h->nvox() * h->KP / 4), 256, 0, h->stream>>>(c, (S *)h->cpad, h->N[0], h->N[1],
+                                                                       h->N[2], h->K, h->KP);
     cudaError_t e = cudaGetLastError();
     prof_end(h, TT_KSLOT_PACK, ev);
     return e;
@@ -83,14 +97,14 @@ template cudaError_t launch_unpack<double>(tt_handle *, const double *, double *
 
 // ------------------------------------------------------------- reductions
 
-// out[0] = (add ? add[0] : 0) + mul * sum(partials[0..n)), fixed order.
+// out[0] = (add ? add[0] : 0) + mul * sum(partials[0..n)), summed in the
+// fixed order of sum_fixed_order (the same as the loss reduction that the
+// adjoint's first CTA performs).
 __global__ void k_reduce(const double *__restrict__ partials, long long n, double *__restrict__ out,
                          const double *__restrict__ add, double mul)
 {
     __shared__ double red[32];
-    double v = 0.0;
-    for (long long t = threadIdx.x; t < n; t += blockDim.x) v += partials[t];
-    v = block_sum(v, red);
+    const double v = sum_fixed_order(partials, n, red);
     if (threadIdx.x == 0) out[0] = (add ? add[0] : 0.0) + mul * v;
 }
 
@@ -99,7 +113,7 @@ cudaError_t launch_reduce(tt_handle *h, const double *partials, long long n, dou
 {
     cudaEvent_t ev;
     prof_begin(h, TT_KSLOT_REDUCE, &ev);
-    k_reduce<<<1, 256, 0, h->stream>>>(partials, n, out, add, mul);
+    k_reduce<<<1, kThreads, 0, h->stream>>>(partials, n, out, add, mul);
     cudaError_t e = cudaGetLastError();
     prof_end(h, TT_KSLOT_REDUCE, ev);
     return e;

@@ -119,6 +119,26 @@ def test_gradient_residual_fp64(kw):
     assert rel_l2(g.cpu().numpy(), g_ref) <= F64_TOL
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_loss_is_the_same_with_and_without_gradient(prec):
+    """The loss partials are reduced by the adjoint's first CTA when a gradient
+    is wanted and by a one-CTA kernel otherwise: both sum in the same fixed
+    order, so the two losses agree bit for bit.  The workload's forward grid
+    (64^3, 120 projections: 7680 CTAs) exercises the eight-way strided sum
+    with a ragged tail."""
+    st = synth.workload("ell64")
+    dt = torch.float32 if prec == "f32" else torch.float64
+    h = tt.Handle(st, prec)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(3)
+    c = torch.randn(st.volume_shape, device="cuda", generator=gen, dtype=dt)
+    I = torch.rand(st.data_shape, device="cuda", generator=gen, dtype=dt)
+    L1, g = h.gradient_residual(c, I, None)
+    L0, _ = h.gradient_residual(c, I, None, want_grad=False)
+    assert L1 == L0
+    assert torch.isfinite(g).all()
+
+
 def test_adjoint_identity_on_gpu_fp64():
     st = synth.small_setup(n=(14, 12, 13), nj=15, nk=17, ell_max=4, n_proj=11, n_seg=6, seed=8)
     h = tt.Handle(st, "f64")
