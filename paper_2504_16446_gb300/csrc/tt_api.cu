@@ -1,5 +1,6 @@
 // tt_api.cu -- C ABI of libtt: validation, geometry set-up (host, FP64),
 // buffer ownership and the orchestration of the kernels on the handle's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -264,6 +265,8 @@ static void free_handle(tt_handle *h)
     cudaFree(h->geo); cudaFree(h->B64); cudaFree(h->Bp); cudaFree(h->cpad); cudaFree(h->gpad);
     cudaFree(h->G); cudaFree(h->partials); cudaFree(h->loss_dev); cudaFree(h->red);
     cudaFree(h->hc); cudaFree(h->hI); cudaFree(h->hW); cudaFree(h->hg);
+    for (cudaEvent_t e : h->chunk_ready) cudaEventDestroy(e);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     if (h->loss_pinned) cudaFreeHost(h->loss_pinned);
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
     for (cudaEvent_t e : h->prof.free_events) cudaEventDestroy(e);
@@ -563,15 +566,46 @@ tt_status tt_gradient_residual_host(tt_handle *h, const float *c_host, const flo
     if (!c_host || !I_host || !g_host || !loss_host)
         return invalid("tt_gradient_residual_host: c, I, g, loss must not be NULL");
     const size_t bc = sizeof(float) * h->nvox() * h->K, bd = sizeof(float) * h->ndata();
+    const int Q = std::min(4, h->S);               // data chunks overlapped with the forward
     if (!h->hc) TT_CUDA(cudaMalloc(&h->hc, bc), "host-path cudaMalloc");
     if (!h->hg) TT_CUDA(cudaMalloc(&h->hg, bc), "host-path cudaMalloc");
     if (!h->hI) TT_CUDA(cudaMalloc(&h->hI, bd), "host-path cudaMalloc");
     if (W_host && !h->hW) TT_CUDA(cudaMalloc(&h->hW, bd), "host-path cudaMalloc");
+    if (!h->copy_stream) TT_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "copy stream");
+    while ((int)h->chunk_ready.size() < Q + 1) {
+        cudaEvent_t e;
+        TT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "chunk event");
+        h->chunk_ready.push_back(e);
+    }
+    // The coefficient volume goes first on the compute stream; the data and
+    // weights follow in Q projection chunks on the copy stream (after any
+    // earlier work on the compute stream), and the forward launch of chunk q
+    // waits only for chunk q.  The gradient then returns on the compute stream.
     TT_CUDA(cudaMemcpyAsync(h->hc, c_host, bc, cudaMemcpyHostToDevice, h->stream), "H2D c");
-    TT_CUDA(cudaMemcpyAsync(h->hI, I_host, bd, cudaMemcpyHostToDevice, h->stream), "H2D I");
-    if (W_host) TT_CUDA(cudaMemcpyAsync(h->hW, W_host, bd, cudaMemcpyHostToDevice, h->stream), "H2D W");
-    st = tt_grad_enqueue<float>(h, (const float *)h->hc, (const float *)h->hI, W_host ? (const float *)h->hW : nullptr,
-                                (float *)h->hg);
+    TT_CUDA(cudaEventRecord(h->chunk_ready[Q], h->stream), "event");
+    TT_CUDA(cudaStreamWaitEvent(h->copy_stream, h->chunk_ready[Q], 0), "stream wait");
+    const size_t per_proj = (size_t)h->nj * h->nk * h->C;
+    for (int q = 0; q < Q; ++q) {
+        const int s0 = (int)((long long)h->S * q / Q), s1 = (int)((long long)h->S * (q + 1) / Q);
+        const size_t off = per_proj * s0, n = per_proj * (s1 - s0);
+        TT_CUDA(cudaMemcpyAsync((float *)h->hI + off, I_host + off, sizeof(float) * n, cudaMemcpyHostToDevice,
+                                h->copy_stream), "H2D I");
+        if (W_host)
+            TT_CUDA(cudaMemcpyAsync((float *)h->hW + off, W_host + off, sizeof(float) * n, cudaMemcpyHostToDevice,
+                                    h->copy_stream), "H2D W");
+        TT_CUDA(cudaEventRecord(h->chunk_ready[q], h->copy_stream), "event");
+    }
+    const float *I = (const float *)h->hI, *W = W_host ? (const float *)h->hW : nullptr;
+    st = with_storage<float>(h, [&]<typename S>() -> tt_status {
+        TT_CUDA((launch_pack<float, S>(h, (const float *)h->hc)), "pack");
+        for (int q = 0; q < Q; ++q) {
+            const int s0 = (int)((long long)h->S * q / Q), s1 = (int)((long long)h->S * (q + 1) / Q);
+            TT_CUDA(cudaStreamWaitEvent(h->stream, h->chunk_ready[q], 0), "stream wait");
+            TT_CUDA((launch_forward<float, S>(h, nullptr, I, W, true, s0, s1)), "forward");
+        }
+        TT_CUDA((launch_adjoint<float, S>(h, (float *)h->hg, true)), "adjoint");
+        return TT_OK;
+    });
     if (st != TT_OK) return st;
     TT_CUDA(cudaMemcpyAsync(g_host, h->hg, bc, cudaMemcpyDeviceToHost, h->stream), "D2H g");
     return tt_read_loss(h, loss_host);

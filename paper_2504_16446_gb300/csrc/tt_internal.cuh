@@ -111,6 +111,8 @@ struct tt_handle {
     double *loss_pinned = nullptr;       // pinned host scalar
     // host-buffer entry point staging (allocated on first use)
     void *hc = nullptr, *hI = nullptr, *hW = nullptr, *hg = nullptr;
+    cudaStream_t copy_stream = nullptr;  // host-buffer path: data chunks copied while the forward runs
+    std::vector<cudaEvent_t> chunk_ready;
     long long launch_count = 0;
     tt::Profile prof;
     std::vector<tt::AdjParams<float>> adj_f32;     // adjoint constants, one block per launch
@@ -150,8 +152,10 @@ template <typename T>
 cudaError_t launch_unpack(tt_handle *h, const T *gpad, T *g);
 // Projector launchers: arithmetic in T, the coefficient volume cpad and the
 // back-contracted residual G stored as S (S = T, or a 2-byte type for T = float).
+// Projections [s0, s1) only (s1 < 0: to the last); the gradient mode writes
+// the loss partials of those projections' CTAs.
 template <typename T, typename S>
-cudaError_t launch_forward(tt_handle *h, T *Iout, const T *I, const T *W, bool grad);
+cudaError_t launch_forward(tt_handle *h, T *Iout, const T *I, const T *W, bool grad, int s0 = 0, int s1 = -1);
 template <typename T, typename S>
 cudaError_t launch_backcontract(tt_handle *h, const T *R);
 // g [nvox][K] (unpadded) = exact-transpose gather of G; S above one

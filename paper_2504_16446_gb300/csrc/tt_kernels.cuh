@@ -299,7 +299,7 @@ template <typename T, typename S, int KP, int LG, bool GRAD>
 __global__ void __launch_bounds__(kThreads)
 k_forward(const ProjGeom *__restrict__ geo, const S *__restrict__ cpad /* interior origin */,
           const T *__restrict__ Bp,
-          int nj, int nk, int C, int CP, int tiles_k, int slab_order,
+          int nj, int nk, int C, int CP, int tiles_k, int slab_order, int s_base,
           T *__restrict__ Iout, const T *__restrict__ Id, const T *__restrict__ Wd,
           S *__restrict__ G, double *__restrict__ partials)
 {
@@ -317,9 +317,11 @@ k_forward(const ProjGeom *__restrict__ geo, const S *__restrict__ cpad /* interi
     // so that the CTAs in flight march the same few detector rows of many
     // projections -- for rotations about the j axis the same y-slab of the
     // volume, which then stays in L2 when the whole volume does not fit.
-    int tk, s, tj;
-    if (slab_order) { tk = blockIdx.x % tiles_k; s = blockIdx.x / tiles_k; tj = blockIdx.y; }
-    else { s = blockIdx.y; tj = blockIdx.x / tiles_k; tk = blockIdx.x % tiles_k; }
+    // The launch covers projections s_base, s_base + 1, ... (all of them, or
+    // one chunk of a pipelined host-buffer evaluation).
+    int tk, s, tj, tiles_j;
+    if (slab_order) { tk = blockIdx.x % tiles_k; s = s_base + blockIdx.x / tiles_k; tj = blockIdx.y; tiles_j = gridDim.y; }
+    else { s = s_base + blockIdx.y; tj = blockIdx.x / tiles_k; tk = blockIdx.x % tiles_k; tiles_j = gridDim.x / tiles_k; }
     const int r = threadIdx.x / LG, q = threadIdx.x % LG;
     const int j = tj * TJ + r / TK, k = tk * TK + r % TK;
     const bool valid = (j < nj) && (k < nk);
@@ -395,7 +397,9 @@ k_forward(const ProjGeom *__restrict__ geo, const S *__restrict__ cpad /* interi
     if constexpr (GRAD) {
         const double lv = (q == 0 && valid) ? (double)lossr : 0.0;
         const double tot = block_sum(lv, red);
-        if (threadIdx.x == 0) partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+        // canonical CTA index (projection, j tile, k tile): the same for
+        // either CTA order and for chunked launches, so the loss sums alike
+        if (threadIdx.x == 0) partials[((long long)s * tiles_j + tj) * tiles_k + tk] = tot;
     }
 }
 
@@ -651,15 +655,17 @@ k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const S *__restrict__ 
 // ------------------------------------------------------------ launchers
 
 template <typename T, typename S, int L>
-cudaError_t launch_forward_L(tt_handle *h, T *Iout, const T *I, const T *W, bool grad)
+cudaError_t launch_forward_L(tt_handle *h, T *Iout, const T *I, const T *W, bool grad, int s0, int s1)
 {
+    if (s1 < 0) s1 = h->S;
+    const int ns = s1 - s0;
     constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K);
     constexpr int RAYS = kThreads / LG, TK = 8, TJ = RAYS / TK;
     const int tiles_k = (h->nk + TK - 1) / TK, tiles_j = (h->nj + TJ - 1) / TJ;
     // slab order once the padded volume would take more than half of L2
     const long long vol_bytes = (long long)(h->N[0] + 4) * (h->N[1] + 4) * (h->N[2] + 4) * KP * sizeof(S);
     const int slab = vol_bytes > (64LL << 20) ? 1 : 0;
-    const dim3 grid = slab ? dim3(tiles_k * h->S, tiles_j) : dim3(tiles_k * tiles_j, h->S);
+    const dim3 grid = slab ? dim3(tiles_k * ns, tiles_j) : dim3(tiles_k * tiles_j, ns);
     const size_t smem = (size_t)h->CP * KP * sizeof(T);
     const T *Bp = (const T *)h->Bp;
     const S *cpad = (const S *)h->cpad + h->cpad_origin * KP;
@@ -668,12 +674,12 @@ cudaError_t launch_forward_L(tt_handle *h, T *Iout, const T *I, const T *W, bool
     if (grad) {
         auto kern = k_forward<T, S, KP, LG, true>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<grid, kThreads, smem, h->stream>>>(h->geo, cpad, Bp, h->nj, h->nk, h->C, h->CP, tiles_k, slab,
+        kern<<<grid, kThreads, smem, h->stream>>>(h->geo, cpad, Bp, h->nj, h->nk, h->C, h->CP, tiles_k, slab, s0,
                                                  nullptr, I, W, (S *)h->G, h->partials);
     } else {
         auto kern = k_forward<T, S, KP, LG, false>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<grid, kThreads, smem, h->stream>>>(h->geo, cpad, Bp, h->nj, h->nk, h->C, h->CP, tiles_k, slab,
+        kern<<<grid, kThreads, smem, h->stream>>>(h->geo, cpad, Bp, h->nj, h->nk, h->C, h->CP, tiles_k, slab, s0,
                                                  Iout, nullptr, nullptr, nullptr, nullptr);
     }
     cudaError_t e = cudaGetLastError();
@@ -726,16 +732,17 @@ cudaError_t launch_adjoint_L(tt_handle *h, T *g, bool reduce_loss)
 // Instantiates the three launchers of one (T, S) pair for every band limit.
 #define TT_INSTANTIATE_PROJECTORS(T, S)                                                        \
     template <>                                                                                \
-    cudaError_t launch_forward<T, S>(tt_handle * h, T * Iout, const T *I, const T *W, bool grad) \
+    cudaError_t launch_forward<T, S>(tt_handle * h, T * Iout, const T *I, const T *W, bool grad, \
+                                     int s0, int s1)                                            \
     {                                                                                          \
         switch (h->L) {                                                                        \
-        case 0: return launch_forward_L<T, S, 0>(h, Iout, I, W, grad);                         \
-        case 2: return launch_forward_L<T, S, 2>(h, Iout, I, W, grad);                         \
-        case 4: return launch_forward_L<T, S, 4>(h, Iout, I, W, grad);                         \
-        case 6: return launch_forward_L<T, S, 6>(h, Iout, I, W, grad);                         \
-        case 8: return launch_forward_L<T, S, 8>(h, Iout, I, W, grad);                         \
-        case 10: return launch_forward_L<T, S, 10>(h, Iout, I, W, grad);                       \
-        case 12: return launch_forward_L<T, S, 12>(h, Iout, I, W, grad);                       \
+        case 0: return launch_forward_L<T, S, 0>(h, Iout, I, W, grad, s0, s1);                 \
+        case 2: return launch_forward_L<T, S, 2>(h, Iout, I, W, grad, s0, s1);                 \
+        case 4: return launch_forward_L<T, S, 4>(h, Iout, I, W, grad, s0, s1);                 \
+        case 6: return launch_forward_L<T, S, 6>(h, Iout, I, W, grad, s0, s1);                 \
+        case 8: return launch_forward_L<T, S, 8>(h, Iout, I, W, grad, s0, s1);                 \
+        case 10: return launch_forward_L<T, S, 10>(h, Iout, I, W, grad, s0, s1);               \
+        case 12: return launch_forward_L<T, S, 12>(h, Iout, I, W, grad, s0, s1);               \
         default: return cudaErrorInvalidValue;                                                 \
         }                                                                                      \
     }                                                                                          \
