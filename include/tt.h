@@ -164,9 +164,14 @@ tt_status tt_gradient_residual(tt_handle *h, const float *c_dev, const float *I_
 tt_status tt_gradient_residual_f64(tt_handle *h, const double *c_dev, const double *I_dev,
                                    const double *W_dev, double *g_dev, double *loss_host);
 
-/* The same evaluation on HOST buffers (c_host, I_host, W_host may be pageable
- * or pinned; W_host may be NULL): copies the inputs to handle-owned device
- * buffers, evaluates, and copies the gradient back to g_host.  Synchronous. */
+/* The same evaluation on HOST buffers (pageable or page-locked; W_host may
+ * be NULL).  The inputs are staged through handle-owned device buffers: c
+ * first, then I and W in up to eight projection chunks copied on a second
+ * stream while the forward projects the chunks already present.  A
+ * page-locked, device-mapped g_host (cudaHostAlloc / cudaMallocHost memory)
+ * is written by the adjoint kernel in place; any other g_host receives the
+ * gradient with one copy.  Same results, bit for bit, as
+ * tt_gradient_residual.  Synchronous. */
 tt_status tt_gradient_residual_host(tt_handle *h, const float *c_host, const float *I_host,
                                     const float *W_host, float *g_host, double *loss_host);
 

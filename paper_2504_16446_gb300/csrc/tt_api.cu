@@ -558,6 +558,18 @@ tt_status tt_gradient_residual_f64(tt_handle *h, const double *c, const double *
     return st != TT_OK ? st : grad_impl<double>(h, c, I, W, g, loss_host);
 }
 
+// Device address of page-locked, device-mapped host memory (the device can
+// load and store it directly over the host link), else NULL.
+static const void *mapped_device_pointer(const void *host)
+{
+    cudaPointerAttributes pa;
+    if (host && cudaPointerGetAttributes(&pa, host) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer)
+        return pa.devicePointer;
+    cudaGetLastError();   // clear the query's error state for unregistered memory
+    return nullptr;
+}
+
 tt_status tt_gradient_residual_host(tt_handle *h, const float *c_host, const float *I_host, const float *W_host,
                                     float *g_host, double *loss_host)
 {
@@ -566,9 +578,17 @@ tt_status tt_gradient_residual_host(tt_handle *h, const float *c_host, const flo
     if (!c_host || !I_host || !g_host || !loss_host)
         return invalid("tt_gradient_residual_host: c, I, g, loss must not be NULL");
     const size_t bc = sizeof(float) * h->nvox() * h->K, bd = sizeof(float) * h->ndata();
-    const int Q = std::min(4, h->S);               // data chunks overlapped with the forward
+    // Inputs go through device staging buffers: c first on the compute
+    // stream, then I and W in Q projection chunks on a copy stream, the
+    // forward launch of chunk q waiting only for chunk q.  (Reading mapped
+    // inputs in place over the host link measured slower than these copies.)
+    // A page-locked, device-mapped g_host is written by the adjoint in place,
+    // its stores crossing the host link while the kernel runs; any other
+    // g_host gets the gradient with one copy.
+    float *g_map = (float *)mapped_device_pointer(g_host);
+    const int Q = std::min(8, h->S);
     if (!h->hc) TT_CUDA(cudaMalloc(&h->hc, bc), "host-path cudaMalloc");
-    if (!h->hg) TT_CUDA(cudaMalloc(&h->hg, bc), "host-path cudaMalloc");
+    if (!g_map && !h->hg) TT_CUDA(cudaMalloc(&h->hg, bc), "host-path cudaMalloc");
     if (!h->hI) TT_CUDA(cudaMalloc(&h->hI, bd), "host-path cudaMalloc");
     if (W_host && !h->hW) TT_CUDA(cudaMalloc(&h->hW, bd), "host-path cudaMalloc");
     if (!h->copy_stream) TT_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "copy stream");
@@ -577,10 +597,6 @@ tt_status tt_gradient_residual_host(tt_handle *h, const float *c_host, const flo
         TT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "chunk event");
         h->chunk_ready.push_back(e);
     }
-    // The coefficient volume goes first on the compute stream; the data and
-    // weights follow in Q projection chunks on the copy stream (after any
-    // earlier work on the compute stream), and the forward launch of chunk q
-    // waits only for chunk q.  The gradient then returns on the compute stream.
     TT_CUDA(cudaMemcpyAsync(h->hc, c_host, bc, cudaMemcpyHostToDevice, h->stream), "H2D c");
     TT_CUDA(cudaEventRecord(h->chunk_ready[Q], h->stream), "event");
     TT_CUDA(cudaStreamWaitEvent(h->copy_stream, h->chunk_ready[Q], 0), "stream wait");
@@ -603,11 +619,11 @@ tt_status tt_gradient_residual_host(tt_handle *h, const float *c_host, const flo
             TT_CUDA(cudaStreamWaitEvent(h->stream, h->chunk_ready[q], 0), "stream wait");
             TT_CUDA((launch_forward<float, S>(h, nullptr, I, W, true, s0, s1)), "forward");
         }
-        TT_CUDA((launch_adjoint<float, S>(h, (float *)h->hg, true)), "adjoint");
+        TT_CUDA((launch_adjoint<float, S>(h, g_map ? g_map : (float *)h->hg, true)), "adjoint");
         return TT_OK;
     });
     if (st != TT_OK) return st;
-    TT_CUDA(cudaMemcpyAsync(g_host, h->hg, bc, cudaMemcpyDeviceToHost, h->stream), "D2H g");
+    if (!g_map) TT_CUDA(cudaMemcpyAsync(g_host, h->hg, bc, cudaMemcpyDeviceToHost, h->stream), "D2H g");
     return tt_read_loss(h, loss_host);
 }
 

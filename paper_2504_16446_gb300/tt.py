@@ -263,10 +263,15 @@ class Handle:
         self._sync_stream()
         if self.precision == "f64":
             raise TypeError("the host entry point takes float arrays")
-        for name, a, shp in (("c", c, self.volume_shape), ("I", I, self.data_shape)):
+        g = np.empty(self.volume_shape, np.float32) if g_out is None else g_out
+        checks = [("c", c, self.volume_shape), ("I", I, self.data_shape), ("g_out", g, self.volume_shape)]
+        if W is not None:
+            checks.append(("W", W, self.data_shape))
+        for name, a, shp in checks:
             if a.dtype != np.float32 or a.shape != shp or not a.flags["C_CONTIGUOUS"]:
                 raise ValueError(f"{name} must be C-contiguous float32 of shape {shp}")
-        g = np.empty(self.volume_shape, np.float32) if g_out is None else g_out
+        if not g.flags["WRITEABLE"]:
+            raise ValueError("g_out must be writeable")
         loss = ctypes.c_double(0.0)
         _check(self.lib.tt_gradient_residual_host(
             self._h, c.ctypes.data_as(_P), I.ctypes.data_as(_P),

@@ -188,6 +188,14 @@ def test_host_entry_point_matches_device_entry_point():
     loss_h, g_h = h.gradient_residual_host(c, I, W)
     assert loss_h == loss_d
     np.testing.assert_array_equal(g_h, g_d.cpu().numpy())
+    # page-locked buffers: the adjoint writes the gradient straight into g_out
+    pin = {k: torch.empty(v.shape, dtype=torch.float32, pin_memory=True) for k, v in (("c", c), ("I", I), ("W", W))}
+    for k, v in (("c", c), ("I", I), ("W", W)):
+        pin[k].numpy()[...] = v
+    g_pin = torch.full(st.volume_shape, float("nan"), dtype=torch.float32, pin_memory=True)
+    loss_p, g_p = h.gradient_residual_host(pin["c"].numpy(), pin["I"].numpy(), pin["W"].numpy(), g_out=g_pin.numpy())
+    assert loss_p == loss_d
+    np.testing.assert_array_equal(g_pin.numpy(), g_d.cpu().numpy())
 
 
 def test_host_entry_point_pipelined_chunks_on_slab_ordered_forward():
