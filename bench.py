@@ -54,6 +54,22 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """Largest x over the ranks of the default process group (x itself when
+    there is none).  The job's wall time is the slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: units every rank processed / the job's time."""
+    return world * units_per_rank / seconds
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -352,13 +368,9 @@ def run_ours(args):
     launches = h.launch_count() - launches0
     prof = h.profile_read()
     h.profile(False)
-    total_ms = sum(times)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(times), dist, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
+    value = job_rate(args.steps, world, total_ms / 1e3)
 
     # e2e through the host-buffer entry point: H2D of c, I, W and D2H of g inside the timed region
     c_h = torch.empty(c.shape, dtype=torch.float32, pin_memory=True)
@@ -376,12 +388,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         h.gradient_residual_host(cn, In, Wn, gn)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_total = max(sum(e2e_t), 1e-12)
-    if dist:
-        t = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * args.e2e_steps / e2e_total if args.e2e_steps > 0 else None
+    e2e_total = max_over_ranks(max(sum(e2e_t), 1e-12), dist, "cuda")
+    e2e_value = job_rate(args.e2e_steps, world, e2e_total) if args.e2e_steps > 0 else None
     h2d = (c.numel() + I.numel() + W.numel()) * 4
     d2h = g.numel() * 4 + 8
 
