@@ -148,12 +148,26 @@ static ProjGeom make_geom(const tt_handle *h, int s)
     const double i00 = g.vk / det, i01 = -g.uk / det, i10 = -g.vj / det, i11 = g.uj / det;
     g.jU = i00; g.jV = i01; g.jP = -(i00 * g.up + i01 * g.vp); g.jc0 = -(i00 * g.u0 + i01 * g.v0);
     g.kU = i10; g.kV = i11; g.kP = -(i10 * g.up + i11 * g.vp); g.kc0 = -(i10 * g.u0 + i11 * g.v0);
-    const double eps = 1e-3;                 // guards the window against rounding of jc, kc
-    g.hj = std::fabs(i00) + std::fabs(i01) + eps;
-    g.hk = std::fabs(i10) + std::fabs(i11) + eps;
-    g.nwj = (int)std::ceil(2.0 * g.hj);
-    g.nwk = (int)std::ceil(2.0 * g.hk);
+    g.hj = std::fabs(i00) + std::fabs(i01);
+    g.hk = std::fabs(i10) + std::fabs(i11);
     return g;
+}
+
+// Number of integers an open interval of length L can hold (L within FP
+// rounding of an integer n counts as n: a point that only rounding puts
+// inside has weight within rounding of zero).
+static int points_in(double L) { return std::max(1, (int)std::ceil(L - 1e-9)); }
+
+// Lower edge of the inner coordinate, relative to the voxel centre, as a
+// function of the outer offset d: the constraint |ci di + co d| < 1 gives
+// di > -1/|ci| - (co/ci) d.  A vanishing ci leaves the inner axis unbounded
+// by this constraint.
+static void inner_edge(double ci, double co, double &offset, double &slope, double &length)
+{
+    if (std::fabs(ci) < 1e-12) { offset = -1e30; slope = 0.0; length = 1e30; return; }
+    offset = -1.0 / std::fabs(ci);
+    slope = -co / ci;
+    length = 2.0 / std::fabs(ci);
 }
 
 template <typename T>
@@ -164,12 +178,36 @@ static AdjProj<T> adj_proj(const ProjGeom &g)
     kc[1 + g.m] += g.kP; kc[1 + g.u] += g.kU; kc[1 + g.v] += g.kV;
     bu[1 + g.m] += g.up; bu[1 + g.u] -= 1.0;
     bv[1 + g.m] += g.vp; bv[1 + g.v] -= 1.0;
+    // the two enumeration orders: outer k / inner j, and outer j / inner k
+    double au[2], lu[2], av[2], lv[2];
+    int no[2], ni[2];
+    for (int t = 0; t < 2; ++t) {
+        const bool outer_j = t == 1;
+        const double ui = outer_j ? g.uk : g.uj, uo = outer_j ? g.uj : g.uk;
+        const double vi = outer_j ? g.vk : g.vj, vo = outer_j ? g.vj : g.vk;
+        double Lu, Lv;
+        inner_edge(ui, uo, au[t], lu[t], Lu);
+        inner_edge(vi, vo, av[t], lv[t], Lv);
+        const double hi = outer_j ? g.hk : g.hj, ho = outer_j ? g.hj : g.hk;
+        no[t] = points_in(2.0 * ho);
+        ni[t] = points_in(std::min(std::min(Lu, Lv), 2.0 * hi));
+    }
+    const int t = (no[1] * ni[1] < no[0] * ni[0]) ? 1 : 0;
+    const bool outer_j = t == 1;
     AdjProj<T> a;
-    for (int t = 0; t < 4; ++t) { a.jc[t] = (T)jc[t]; a.kc[t] = (T)kc[t]; a.bu[t] = (T)bu[t]; a.bv[t] = (T)bv[t]; }
-    a.uj = (T)g.uj; a.uk = (T)g.uk; a.vj = (T)g.vj; a.vk = (T)g.vk;
-    a.hj = (T)g.hj; a.hk = (T)g.hk; a.step = (T)g.step;
-    a.nwj = g.nwj; a.nwk = g.nwk;
-    a.shape = (g.nwj <= 3 && g.nwk <= 3) ? 16 * g.nwj + g.nwk : 0;
+    for (int i = 0; i < 4; ++i) {
+        a.oc[i] = (T)(outer_j ? jc[i] : kc[i]);
+        a.ic[i] = (T)(outer_j ? kc[i] : jc[i]);
+        a.bu[i] = (T)bu[i];
+        a.bv[i] = (T)bv[i];
+    }
+    a.uo = (T)(outer_j ? g.uj : g.uk); a.ui = (T)(outer_j ? g.uk : g.uj);
+    a.vo = (T)(outer_j ? g.vj : g.vk); a.vi = (T)(outer_j ? g.vk : g.vj);
+    a.ho = (T)(outer_j ? g.hj : g.hk);
+    a.au = (T)au[t]; a.lu = (T)lu[t]; a.av = (T)av[t]; a.lv = (T)lv[t];
+    a.step = (T)g.step;
+    a.shape = (no[t] <= 3 && ni[t] <= 3) ? 16 * no[t] + ni[t] : 0;
+    a.order = no[t] | (ni[t] << 8) | ((outer_j ? 1 : 0) << 16);
     return a;
 }
 
@@ -243,6 +281,8 @@ tt_status validate(const tt_problem *P)
             return invalid("every segment needs finite seg_end > seg_start");
     if (!(P->voxel_size > 0) || !(P->step_size > 0) || !std::isfinite(P->voxel_size) || !std::isfinite(P->step_size))
         return invalid("voxel_size and step_size must be positive and finite");
+    if (P->step_size < 0.02 * P->voxel_size)
+        return invalid("step_size (detector pixel) must be at least 1/50 of voxel_size");
     if (!std::isfinite(P->two_theta)) return invalid("two_theta must be finite");
     const tt_frame &f = P->frame;
     const double *unit[5] = {f.p, f.j, f.k, f.q0, f.q90};

@@ -48,23 +48,28 @@ struct ProjGeom {
     double step;              // a / |p_s,m|
     double jc0, jU, jV, jP;
     double kc0, kU, kV, kP;
-    double hj, hk;
+    double hj, hk;            // half extents in j and k of the rays around a voxel (|du|, |dv| < 1)
     int m, u, v;              // main and transverse axes (0=x, 1=y, 2=z)
     int Nm, Nu, Nv;
     int sm, su, sv;           // strides of the axes in the padded volume cpad
-    int nwj, nwk;
 };
 
-// Per-projection constants of the adjoint gather in the element type, as
-// affine functions of the voxel indices (x, y, z):
-//   jc = jc[0] + jc[1] x + jc[2] y + jc[3] z        (likewise kc)
-//   du(j,k) = bu(x,y,z) + j uj + k uk,  dv(j,k) = bv(x,y,z) + j vj + k vk
-// shape = 16 * nwj + nwk (window of candidate rays).
+// Per-projection constants of the adjoint gather in the element type.  The
+// candidate rays of a voxel are enumerated over an outer detector axis o and
+// an inner axis i ((o, i) = (k, j), or (j, k) when bit 16 of order is set):
+//   oc = oc[0] + oc[1] x + oc[2] y + oc[3] z   continuous outer coordinate of
+//                                              the voxel centre (likewise ic)
+//   du(o,i) = bu(x,y,z) + o uo + i ui,  dv(o,i) = bv(x,y,z) + o vo + i vi
+//   columns o = o0 ... o0 + NO - 1,  o0 = floor(oc - ho) + 1
+//   column o: i = i0 ... i0 + NI - 1,
+//             i0 = floor(ic + max(au + lu (o - oc), av + lv (o - oc))) + 1
+// shape = 16 * NO + NI when both are <= 3 (unrolled loops), else 0;
+// order = NO | NI << 8 | outer_is_j << 16.
 template <typename T>
 struct AdjProj {
-    T jc[4], kc[4], bu[4], bv[4];
-    T uj, uk, vj, vk, hj, hk, step;
-    int shape, nwj, nwk;
+    T oc[4], ic[4], bu[4], bv[4];
+    T uo, ui, vo, vi, ho, au, lu, av, lv, step;
+    int shape, order;
 };
 
 // Kernel-parameter block holding the constants of up to kMax projections
