@@ -307,6 +307,8 @@ static void free_handle(tt_handle *h)
     cudaFree(h->hc); cudaFree(h->hI); cudaFree(h->hW); cudaFree(h->hg);
     for (cudaEvent_t e : h->chunk_ready) cudaEventDestroy(e);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    for (cudaStream_t t : h->side)
+        if (t) cudaStreamDestroy(t);
     if (h->loss_pinned) cudaFreeHost(h->loss_pinned);
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
     for (cudaEvent_t e : h->prof.free_events) cudaEventDestroy(e);
@@ -619,9 +621,11 @@ tt_status tt_gradient_residual_host(tt_handle *h, const float *c_host, const flo
         return invalid("tt_gradient_residual_host: c, I, g, loss must not be NULL");
     const size_t bc = sizeof(float) * h->nvox() * h->K, bd = sizeof(float) * h->ndata();
     // Inputs go through device staging buffers: c first on the compute
-    // stream, then I and W in Q projection chunks on a copy stream, the
-    // forward launch of chunk q waiting only for chunk q.  (Reading mapped
-    // inputs in place over the host link measured slower than these copies.)
+    // stream, then I and W in Q projection chunks on a copy stream.  The
+    // forward launch of chunk q waits only for chunk q and runs on one of two
+    // side streams, so that a chunk's last wave overlaps the next chunk's
+    // first; the adjoint joins both.  (Reading mapped inputs in place over
+    // the host link measured slower than these copies.)
     // A page-locked, device-mapped g_host is written by the adjoint in place,
     // its stores crossing the host link while the kernel runs; any other
     // g_host gets the gradient with one copy.
@@ -632,7 +636,9 @@ tt_status tt_gradient_residual_host(tt_handle *h, const float *c_host, const flo
     if (!h->hI) TT_CUDA(cudaMalloc(&h->hI, bd), "host-path cudaMalloc");
     if (W_host && !h->hW) TT_CUDA(cudaMalloc(&h->hW, bd), "host-path cudaMalloc");
     if (!h->copy_stream) TT_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "copy stream");
-    while ((int)h->chunk_ready.size() < Q + 1) {
+    for (cudaStream_t &t : h->side)
+        if (!t) TT_CUDA(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking), "side stream");
+    while ((int)h->chunk_ready.size() < Q + 4) {
         cudaEvent_t e;
         TT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "chunk event");
         h->chunk_ready.push_back(e);
@@ -652,12 +658,24 @@ tt_status tt_gradient_residual_host(tt_handle *h, const float *c_host, const flo
         TT_CUDA(cudaEventRecord(h->chunk_ready[q], h->copy_stream), "event");
     }
     const float *I = (const float *)h->hI, *W = W_host ? (const float *)h->hW : nullptr;
+    cudaEvent_t packed = h->chunk_ready[Q + 1], side_done[2] = {h->chunk_ready[Q + 2], h->chunk_ready[Q + 3]};
+    const cudaStream_t main_stream = h->stream;
     st = with_storage<float>(h, [&]<typename S>() -> tt_status {
         TT_CUDA((launch_pack<float, S>(h, (const float *)h->hc)), "pack");
-        for (int q = 0; q < Q; ++q) {
+        TT_CUDA(cudaEventRecord(packed, main_stream), "event");
+        for (int t = 0; t < 2; ++t) TT_CUDA(cudaStreamWaitEvent(h->side[t], packed, 0), "stream wait");
+        cudaError_t e = cudaSuccess;
+        for (int q = 0; q < Q && e == cudaSuccess; ++q) {
             const int s0 = (int)((long long)h->S * q / Q), s1 = (int)((long long)h->S * (q + 1) / Q);
-            TT_CUDA(cudaStreamWaitEvent(h->stream, h->chunk_ready[q], 0), "stream wait");
-            TT_CUDA((launch_forward<float, S>(h, nullptr, I, W, true, s0, s1)), "forward");
+            e = cudaStreamWaitEvent(h->side[q & 1], h->chunk_ready[q], 0);
+            h->stream = h->side[q & 1];          // the launcher enqueues on h->stream
+            if (e == cudaSuccess) e = launch_forward<float, S>(h, nullptr, I, W, true, s0, s1);
+            h->stream = main_stream;
+        }
+        TT_CUDA(e, "forward");
+        for (int t = 0; t < 2; ++t) {
+            TT_CUDA(cudaEventRecord(side_done[t], h->side[t]), "event");
+            TT_CUDA(cudaStreamWaitEvent(main_stream, side_done[t], 0), "stream wait");
         }
         TT_CUDA((launch_adjoint<float, S>(h, g_map ? g_map : (float *)h->hg, true)), "adjoint");
         return TT_OK;

@@ -117,6 +117,7 @@ struct tt_handle {
     // host-buffer entry point staging (allocated on first use)
     void *hc = nullptr, *hI = nullptr, *hW = nullptr, *hg = nullptr;
     cudaStream_t copy_stream = nullptr;  // host-buffer path: data chunks copied while the forward runs
+    cudaStream_t side[2] = {nullptr, nullptr};  // host-buffer path: forward chunks, two at a time
     std::vector<cudaEvent_t> chunk_ready;
     long long launch_count = 0;
     tt::Profile prof;
