@@ -133,6 +133,30 @@ struct tt_handle {
 
 namespace tt {
 
+// Compensated FP32 dot-product accumulation (Ogita, Rump & Oishi, "Accurate
+// sum and dot product", SIAM J. Sci. Comput. 26, 2005, algorithm Dot2): the
+// rounding error of each product comes from an FMA, that of each sum from
+// TwoSum, and both are gathered in a second FP32 word.  The result is about
+// as accurate as the dot product summed in twice the working precision, at
+// FP32 speed (this GPU's FP64 rate is a small fraction of its FP32 rate).
+// The _rn intrinsics keep the compiler from contracting the steps.
+struct Dot2 {
+    float s, c;
+};
+
+__device__ __forceinline__ void dot2_add(Dot2 &a, float x, float y)
+{
+    const float p = __fmul_rn(x, y);
+    const float pe = __fmaf_rn(x, y, -p);          // x y - p, exactly
+    const float t = __fadd_rn(a.s, p);
+    const float z = __fsub_rn(t, a.s);
+    const float e = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, z)), __fsub_rn(p, z));   // a.s + p - t, exactly
+    a.s = t;
+    a.c = __fadd_rn(a.c, __fadd_rn(e, pe));
+}
+
+__device__ __forceinline__ double dot2_value(const Dot2 &a) { return (double)a.s + (double)a.c; }
+
 void set_error(const std::string &msg);
 tt_status cuda_fail(cudaError_t e, const char *what);
 // Problem validation and Gauss-Legendre rule shared by the entry points.

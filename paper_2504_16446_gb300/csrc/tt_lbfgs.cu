@@ -1,10 +1,21 @@
 // tt_lbfgs.cu -- device-resident L-BFGS (Section "Optimization"): two-loop
 // recursion (Nocedal & Wright, Algorithm 7.4, H_0 = gamma I with gamma =
-// s.y / y.y of the newest pair), backtracking Armijo line search.  Vectors are
-// in the handle's precision; every dot product is accumulated in FP64 and
-// the recursion coefficients stay on the device (no host round trip inside
-// the two loops).  The host reads back only the loss of each trial point,
-// g.d, and the three dot products that decide whether a pair is stored.
+// s.y / y.y of the newest pair), backtracking Armijo line search.
+//
+// The recursion runs on the Gram matrix of its basis vectors instead of on
+// the vectors themselves (the vector-free formulation of Chen, Wang & Zhou,
+// NIPS 2014): every vector the two loops produce is a linear combination of
+// b = (s_0 .. s_{m-1}, y_0 .. y_{m-1}, g), so each dot product they need is
+// a combination of entries of the FP64 Gram matrix b_i . b_j, and the
+// direction is d = -sum_i c_i b_i for coefficients computed on the host.
+// Per iteration the vectors are touched by three kernels: one forms d and
+// the first trial point, one forms the new pair s = x_t - x, y = g_t - g with
+// its six dot products, one takes the dot products of the new pair and the
+// new gradient with the stored pairs.  The recursion itself -- the same
+// arithmetic as the two loops, in exact arithmetic -- costs O(m^2) on the
+// host.  Dot products of float vectors use compensated FP32 accumulation
+// (Dot2) per thread and FP64 across threads; double vectors use FP64.
+#include <algorithm>
 #include <cmath>
 #include <utility>
 #include <vector>
@@ -17,49 +28,325 @@ tt_status tt_read_loss(tt_handle *h, double *loss_host);
 
 using namespace tt;
 
-struct tt_lbfgs {
-    tt_handle *h = nullptr;
-    int m = 0;
-    long long n = 0;
-    void *x = nullptr, *g = nullptr, *d = nullptr, *xt = nullptr, *gt = nullptr, *ss = nullptr, *ys = nullptr;
-    std::vector<void *> S, Y;
-    std::vector<double> rho, sy, yy;
-    int count = 0, head = -1;
-    double f = 0.0;
-    const void *I = nullptr, *W = nullptr;
-    double *scal = nullptr;       // device: alpha[m], coef[m], misc[8]
-    double *partials = nullptr;   // device: kDotBlocks
-    double *pinned = nullptr;     // host: misc[8]
-};
-
 #define TT_CUDA(call, what)                                          \
     do {                                                             \
         cudaError_t _e = (call);                                     \
         if (_e != cudaSuccess) return ::tt::cuda_fail(_e, what);     \
     } while (0)
 
+namespace {
+
+constexpr int kMaxM = 64;
+constexpr int kPairBlocks = 304;   // CTAs of the pair / cross dot kernels (2 x 152 SMs)
+
+// Blocks of the per-element kernels: a multiple of the SM count, capped.
+unsigned elem_blocks(long long n)
+{
+    long long b = (n + 255) / 256;
+    return (unsigned)std::max(1LL, std::min(b, 152LL * 16));
+}
+
+// Block sum of a double, result on thread 0 (blockDim 256).
+__device__ __forceinline__ double block_total(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = l < (int)(blockDim.x >> 5) ? red[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    return t;
+}
+
+// Linear combination of up to 2 kMaxM + 1 vectors (kernel parameters).
+template <typename T>
+struct Combo {
+    const T *v[2 * kMaxM + 1];
+    double c[2 * kMaxM + 1];
+    int n;
+};
+
+// d = sum_i c_i v_i (in T, coefficients rounded to T), xt = x + a d.
+template <typename T>
+__global__ void k_direction(const __grid_constant__ Combo<T> cb, const T *__restrict__ x, T *__restrict__ d,
+                            T *__restrict__ xt, double a, long long n)
+{
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        T s = T(0);
+        for (int i = 0; i < cb.n; ++i) s = fma((T)cb.c[i], cb.v[i][t], s);
+        d[t] = s;
+        xt[t] = x[t] + (T)a * s;
+    }
+}
+
+// Dot-product accumulator: compensated FP32 for float vectors, FP64 otherwise.
+template <typename T>
+struct Acc {
+    double v = 0.0;
+    __device__ void add(T x, T y) { v = fma(x, y, v); }
+    __device__ double value() const { return v; }
+};
+template <>
+struct Acc<float> {
+    Dot2 a = {0.f, 0.f};
+    __device__ void add(float x, float y) { dot2_add(a, x, y); }
+    __device__ double value() const { return dot2_value(a); }
+};
+
+// xt = x + a d
+template <typename T>
+__global__ void k_trial(const T *__restrict__ x, const T *__restrict__ d, T *__restrict__ xt, double a, long long n)
+{
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x)
+        xt[t] = x[t] + (T)a * d[t];
+}
+
+// s = xt - x, y = gt - g (stored), and per-CTA partials of
+// s.s, s.y, y.y, gt.s, gt.y, gt.gt at part[k * gridDim.x + blockIdx.x].
+template <typename T>
+__global__ void k_pair(const T *__restrict__ x, const T *__restrict__ xt, const T *__restrict__ g,
+                       const T *__restrict__ gt, T *__restrict__ s_out, T *__restrict__ y_out, long long n,
+                       double *__restrict__ part)
+{
+    __shared__ double red[32];
+    Acc<T> acc[6];
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const T s = xt[t] - x[t], y = gt[t] - g[t];
+        const T gn = gt[t];
+        s_out[t] = s;
+        y_out[t] = y;
+        acc[0].add(s, s);
+        acc[1].add(s, y);
+        acc[2].add(y, y);
+        acc[3].add(gn, s);
+        acc[4].add(gn, y);
+        acc[5].add(gn, gn);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double v = block_total(acc[k].value(), red);
+        if (threadIdx.x == 0) part[k * gridDim.x + blockIdx.x] = v;
+    }
+}
+
+// Dot products of the new pair (s, y) and the new gradient gt with stored
+// pair j = slots[blockIdx.y]: s.S_j, s.Y_j, y.S_j, y.Y_j, gt.S_j, gt.Y_j.
+template <typename T>
+struct Slots {
+    const T *S[kMaxM];
+    const T *Y[kMaxM];
+};
+
+template <typename T>
+__global__ void k_cross(const __grid_constant__ Slots<T> sl, const T *__restrict__ s, const T *__restrict__ y,
+                        const T *__restrict__ gt, long long n, double *__restrict__ part)
+{
+    __shared__ double red[32];
+    const T *Sj = sl.S[blockIdx.y], *Yj = sl.Y[blockIdx.y];
+    Acc<T> acc[6];
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const T a = Sj[t], b = Yj[t];
+        const T sv = s[t], yv = y[t], gv = gt[t];
+        acc[0].add(sv, a);
+        acc[1].add(sv, b);
+        acc[2].add(yv, a);
+        acc[3].add(yv, b);
+        acc[4].add(gv, a);
+        acc[5].add(gv, b);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double v = block_total(acc[k].value(), red);
+        if (threadIdx.x == 0) part[((size_t)blockIdx.y * 6 + k) * gridDim.x + blockIdx.x] = v;
+    }
+}
+
+// out[r] = sum of part[r * nb .. r * nb + nb) in a fixed order (one CTA per row).
+__global__ void k_rows(const double *__restrict__ part, int nb, double *__restrict__ out)
+{
+    __shared__ double red[32];
+    double v = 0.0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) v += part[(size_t)blockIdx.x * nb + t];
+    v = block_total(v, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = v;
+}
+
+}  // namespace
+
+struct tt_lbfgs {
+    tt_handle *h = nullptr;
+    int m = 0;
+    long long n = 0;
+    void *slab = nullptr;         // one allocation holding every vector below
+    void *x = nullptr, *g = nullptr, *d = nullptr, *xt = nullptr, *gt = nullptr, *ss = nullptr, *ys = nullptr;
+    std::vector<void *> S, Y;
+    int count = 0, head = -1;     // stored pairs; slot of the newest
+    double f = 0.0;
+    const void *I = nullptr, *W = nullptr;
+    // Gram matrix of b = (S_0..S_{m-1}, Y_0..Y_{m-1}, g), (2m+1)^2, FP64
+    std::vector<double> gram;
+    double *part = nullptr;       // device partials
+    double *dots = nullptr;       // device row sums
+    double *pinned = nullptr;     // host copy of dots
+    int nb = 2 * kMaxM + 1;
+    double &G(int i, int j) { return gram[(size_t)i * nb + j]; }
+    int iS(int slot) const { return slot; }
+    int iY(int slot) const { return m + slot; }
+    int ig() const { return 2 * m; }
+};
+
 static void free_state(tt_lbfgs *st)
 {
     if (!st) return;
-    cudaFree(st->x); cudaFree(st->g); cudaFree(st->d); cudaFree(st->xt); cudaFree(st->gt);
-    cudaFree(st->ss); cudaFree(st->ys);
-    for (void *p : st->S) cudaFree(p);
-    for (void *p : st->Y) cudaFree(p);
-    cudaFree(st->scal); cudaFree(st->partials);
+    cudaFree(st->slab);
+    cudaFree(st->part); cudaFree(st->dots);
     if (st->pinned) cudaFreeHost(st->pinned);
     delete st;
 }
 
-// misc slots in scal[2m + t]
-enum { M_GD = 0, M_GG = 1, M_SY = 2, M_SS = 3, M_YY = 4 };
+// Two-loop recursion on the Gram matrix: coefficients c of d = sum c_i b_i
+// and g.d.  Without stored pairs d = -g.
+static void direction_coeffs(tt_lbfgs *st, std::vector<double> &c, double &gd)
+{
+    const int nb = st->nb, m = st->m;
+    c.assign(nb, 0.0);
+    c[st->ig()] = 1.0;                                   // q = g
+    std::vector<double> alpha(m, 0.0);
+    auto dot_with = [&](int row) {                       // b_row . (sum c_i b_i)
+        double v = 0.0;
+        for (int i = 0; i < nb; ++i)
+            if (c[i] != 0.0) v += c[i] * st->G(row, i);
+        return v;
+    };
+    for (int t = 0; t < st->count; ++t) {               // newest -> oldest
+        const int i = (st->head - t + m) % m;
+        const double rho = 1.0 / st->G(st->iS(i), st->iY(i));
+        alpha[i] = rho * dot_with(st->iS(i));
+        c[st->iY(i)] -= alpha[i];
+    }
+    if (st->count > 0) {
+        const int h = st->head;
+        const double gamma = st->G(st->iS(h), st->iY(h)) / st->G(st->iY(h), st->iY(h));
+        for (double &v : c) v *= gamma;
+    }
+    for (int t = st->count - 1; t >= 0; --t) {          // oldest -> newest
+        const int i = (st->head - t + m) % m;
+        const double rho = 1.0 / st->G(st->iS(i), st->iY(i));
+        const double beta = rho * dot_with(st->iY(i));
+        c[st->iS(i)] += alpha[i] - beta;
+    }
+    for (double &v : c) v = -v;                          // d = -r
+    gd = dot_with(st->ig());
+}
 
 template <typename T>
-static tt_status read_misc(tt_lbfgs *st, int first, int count)
+static tt_status enqueue_direction(tt_lbfgs *st, const std::vector<double> &c, double a)
 {
     tt_handle *h = st->h;
-    TT_CUDA(cudaMemcpyAsync(st->pinned + first, st->scal + 2 * st->m + first, sizeof(double) * count,
-                            cudaMemcpyDeviceToHost, h->stream), "lbfgs scalar copy");
+    Combo<T> cb;
+    cb.n = 0;
+    for (int i = 0; i < st->nb; ++i) {
+        if (c[i] == 0.0) continue;
+        const int m = st->m;
+        cb.v[cb.n] = (const T *)(i == st->ig() ? st->g : (i < m ? st->S[i] : st->Y[i - m]));
+        cb.c[cb.n] = c[i];
+        ++cb.n;
+    }
+    cudaEvent_t ev;
+    prof_begin(h, TT_KSLOT_VECTOR, &ev);
+    k_direction<T><<<elem_blocks(st->n), 256, 0, h->stream>>>(cb, (const T *)st->x, (T *)st->d, (T *)st->xt, a,
+                                                             st->n);
+    cudaError_t e = cudaGetLastError();
+    prof_end(h, TT_KSLOT_VECTOR, ev);
+    TT_CUDA(e, "lbfgs direction");
+    return TT_OK;
+}
+
+template <typename T>
+static tt_status enqueue_trial(tt_lbfgs *st, double a)
+{
+    tt_handle *h = st->h;
+    cudaEvent_t ev;
+    prof_begin(h, TT_KSLOT_VECTOR, &ev);
+    k_trial<T><<<elem_blocks(st->n), 256, 0, h->stream>>>((const T *)st->x, (const T *)st->d, (T *)st->xt, a, st->n);
+    cudaError_t e = cudaGetLastError();
+    prof_end(h, TT_KSLOT_VECTOR, ev);
+    TT_CUDA(e, "lbfgs trial point");
+    return TT_OK;
+}
+
+// Accepted step: new pair into scratch, its dot products and those of the
+// new gradient with every stored pair, one read back.  Then the Gram matrix
+// is updated, the pair stored if the curvature condition holds, and x, g
+// advance.
+template <typename T>
+static tt_status accept_step(tt_lbfgs *st)
+{
+    tt_handle *h = st->h;
+    const int m = st->m;
+    std::vector<int> used;
+    for (int t = 0; t < st->count; ++t) used.push_back((st->head - t + m) % m);
+    const int nu = (int)used.size();
+    cudaEvent_t ev;
+    prof_begin(h, TT_KSLOT_VECTOR, &ev);
+    k_pair<T><<<kPairBlocks, 256, 0, h->stream>>>((const T *)st->x, (const T *)st->xt, (const T *)st->g,
+                                                (const T *)st->gt, (T *)st->ss, (T *)st->ys, st->n, st->part);
+    if (nu > 0) {
+        Slots<T> sl;
+        for (int u = 0; u < nu; ++u) { sl.S[u] = (const T *)st->S[used[u]]; sl.Y[u] = (const T *)st->Y[used[u]]; }
+        k_cross<T><<<dim3(kPairBlocks, nu), 256, 0, h->stream>>>(sl, (const T *)st->ss, (const T *)st->ys,
+                                                               (const T *)st->gt, st->n, st->part + 6 * kPairBlocks);
+    }
+    const int rows = 6 + 6 * nu;
+    k_rows<<<rows, 256, 0, h->stream>>>(st->part, kPairBlocks, st->dots);
+    cudaError_t e = cudaGetLastError();
+    prof_end(h, TT_KSLOT_VECTOR, ev);
+    TT_CUDA(e, "lbfgs pair dots");
+    TT_CUDA(cudaMemcpyAsync(st->pinned, st->dots, sizeof(double) * rows, cudaMemcpyDeviceToHost, h->stream),
+            "lbfgs dots copy");
     TT_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    const double *P = st->pinned;
+    const double ss = P[0], sy = P[1], yy = P[2], gs = P[3], gy = P[4], gg = P[5];
+    const int ig = st->ig();
+    // new gradient against the stored pairs
+    for (int u = 0; u < nu; ++u) {
+        const int j = used[u];
+        st->G(ig, st->iS(j)) = st->G(st->iS(j), ig) = P[6 + 6 * u + 4];
+        st->G(ig, st->iY(j)) = st->G(st->iY(j), ig) = P[6 + 6 * u + 5];
+    }
+    st->G(ig, ig) = gg;
+    if (sy > 1e-10 * std::sqrt(ss) * std::sqrt(yy)) {
+        const int k = (st->head + 1) % m;                 // slot of the new pair (oldest one if full)
+        std::swap(st->S[k], st->ss);
+        std::swap(st->Y[k], st->ys);
+        if (st->count < m) ++st->count;
+        st->head = k;
+        const int sk = st->iS(k), yk = st->iY(k);
+        for (int u = 0; u < nu; ++u) {
+            const int j = used[u];
+            if (j == k) continue;                          // the replaced pair
+            const double *r = P + 6 + 6 * u;
+            st->G(sk, st->iS(j)) = st->G(st->iS(j), sk) = r[0];
+            st->G(sk, st->iY(j)) = st->G(st->iY(j), sk) = r[1];
+            st->G(yk, st->iS(j)) = st->G(st->iS(j), yk) = r[2];
+            st->G(yk, st->iY(j)) = st->G(st->iY(j), yk) = r[3];
+        }
+        st->G(sk, sk) = ss;
+        st->G(sk, yk) = st->G(yk, sk) = sy;
+        st->G(yk, yk) = yy;
+        st->G(ig, sk) = st->G(sk, ig) = gs;
+        st->G(ig, yk) = st->G(yk, ig) = gy;
+    }
+    std::swap(st->x, st->xt);
+    std::swap(st->g, st->gt);
     return TT_OK;
 }
 
@@ -67,41 +354,17 @@ template <typename T>
 static tt_status lbfgs_step(tt_lbfgs *st, double *loss_out, int *n_evals_out)
 {
     tt_handle *h = st->h;
-    const long long n = st->n;
-    T *x = (T *)st->x, *g = (T *)st->g, *d = (T *)st->d;
-    double *alpha = st->scal, *coef = st->scal + st->m, *misc = st->scal + 2 * st->m;
+    std::vector<double> c;
+    double gd = 0.0;
+    direction_coeffs(st, c, gd);
     double step0 = 1.0;
-    bool steepest = st->count == 0;
-    if (!steepest) {
-        // d = g; first loop newest -> oldest
-        TT_CUDA(vec_axpby<T>(h, d, g, n, 1.0, nullptr, 0.0), "lbfgs copy");
-        for (int t = 0; t < st->count; ++t) {
-            const int i = (st->head - t + st->m) % st->m;
-            TT_CUDA(vec_dot<T>(h, (const T *)st->S[i], d, n, st->partials, alpha + i, nullptr, st->rho[i]), "dot");
-            TT_CUDA(vec_axpby<T>(h, d, (const T *)st->Y[i], n, -1.0, alpha + i, 1.0), "axpy");
-        }
-        const double gamma = st->sy[st->head] / st->yy[st->head];
-        TT_CUDA(vec_axpby<T>(h, d, d, n, 0.0, nullptr, gamma), "scale");
-        for (int t = st->count - 1; t >= 0; --t) {
-            const int i = (st->head - t + st->m) % st->m;
-            TT_CUDA(vec_dot<T>(h, (const T *)st->Y[i], d, n, st->partials, coef + i, alpha + i, -st->rho[i]), "dot");
-            TT_CUDA(vec_axpby<T>(h, d, (const T *)st->S[i], n, 1.0, coef + i, 1.0), "axpy");
-        }
-        TT_CUDA(vec_axpby<T>(h, d, d, n, 0.0, nullptr, -1.0), "negate");
-        TT_CUDA(vec_dot<T>(h, g, d, n, st->partials, misc + M_GD, nullptr, 1.0), "dot");
-        tt_status s = read_misc<T>(st, M_GD, 1);
-        if (s != TT_OK) return s;
-        if (!(st->pinned[M_GD] < 0.0)) steepest = true;   // not a descent direction: clear the memory
-    }
-    double gd;
-    if (steepest) {
+    if (st->count > 0 && !(gd < 0.0)) {                  // not a descent direction: clear the memory
         st->count = 0;
         st->head = -1;
-        TT_CUDA(vec_axpby<T>(h, d, g, n, -1.0, nullptr, 0.0), "lbfgs -g");
-        TT_CUDA(vec_dot<T>(h, g, g, n, st->partials, misc + M_GG, nullptr, 1.0), "dot");
-        tt_status s = read_misc<T>(st, M_GG, 1);
-        if (s != TT_OK) return s;
-        const double gg = st->pinned[M_GG];
+        direction_coeffs(st, c, gd);
+    }
+    if (st->count == 0) {
+        const double gg = st->G(st->ig(), st->ig());
         if (!(gg > 0.0) || !std::isfinite(gg)) {
             // stationary point (or non-finite gradient): nothing to do
             if (loss_out) *loss_out = st->f;
@@ -111,45 +374,26 @@ static tt_status lbfgs_step(tt_lbfgs *st, double *loss_out, int *n_evals_out)
         }
         step0 = 1.0 / std::sqrt(gg);
         gd = -gg;
-    } else {
-        gd = st->pinned[M_GD];
     }
 
     const double c1 = 1e-4;
     const int max_evals = 20;
     double a = step0;
-    T *xt = (T *)st->xt, *gt = (T *)st->gt;
+    tt_status s = enqueue_direction<T>(st, c, a);
+    if (s != TT_OK) return s;
     for (int ne = 1; ne <= max_evals; ++ne) {
-        TT_CUDA(cudaMemcpyAsync(xt, x, sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream), "copy x");
-        TT_CUDA(vec_axpby<T>(h, xt, d, n, a, nullptr, 1.0), "trial point");
-        tt_status s = tt_grad_enqueue<T>(h, xt, (const T *)st->I, (const T *)st->W, gt);
+        if (ne > 1) {
+            s = enqueue_trial<T>(st, a);
+            if (s != TT_OK) return s;
+        }
+        s = tt_grad_enqueue<T>(h, (const T *)st->xt, (const T *)st->I, (const T *)st->W, (T *)st->gt);
         if (s != TT_OK) return s;
         double ft = 0.0;
         s = tt_read_loss(h, &ft);
         if (s != TT_OK && s != TT_NONFINITE) return s;
         if (s == TT_OK && ft <= st->f + c1 * a * gd) {
-            // s = xt - x, y = gt - g into scratch; keep the pair only if curvature holds
-            T *sv = (T *)st->ss, *yv = (T *)st->ys;
-            TT_CUDA(vec_sub<T>(h, sv, xt, x, n), "s");
-            TT_CUDA(vec_sub<T>(h, yv, gt, g, n), "y");
-            TT_CUDA(vec_dot<T>(h, sv, yv, n, st->partials, misc + M_SY, nullptr, 1.0), "dot");
-            TT_CUDA(vec_dot<T>(h, sv, sv, n, st->partials, misc + M_SS, nullptr, 1.0), "dot");
-            TT_CUDA(vec_dot<T>(h, yv, yv, n, st->partials, misc + M_YY, nullptr, 1.0), "dot");
-            s = read_misc<T>(st, M_SY, 3);
+            s = accept_step<T>(st);
             if (s != TT_OK) return s;
-            const double sy = st->pinned[M_SY], ss = st->pinned[M_SS], yy = st->pinned[M_YY];
-            if (sy > 1e-10 * std::sqrt(ss) * std::sqrt(yy)) {
-                const int slot = (st->head + 1) % st->m;
-                std::swap(st->S[slot], st->ss);
-                std::swap(st->Y[slot], st->ys);
-                st->rho[slot] = 1.0 / sy;
-                st->sy[slot] = sy;
-                st->yy[slot] = yy;
-                st->head = slot;
-                if (st->count < st->m) ++st->count;
-            }
-            std::swap(st->x, st->xt);
-            std::swap(st->g, st->gt);
             st->f = ft;
             if (loss_out) *loss_out = ft;
             if (n_evals_out) *n_evals_out = ne;
@@ -163,41 +407,53 @@ static tt_status lbfgs_step(tt_lbfgs *st, double *loss_out, int *n_evals_out)
     return TT_LINESEARCH_FAILED;
 }
 
+template <typename T>
+static tt_status initial_gram(tt_lbfgs *st)
+{
+    tt_handle *h = st->h;
+    TT_CUDA((vec_dot<T>(h, (const T *)st->g, (const T *)st->g, st->n, st->part, st->dots, nullptr, 1.0)),
+            "lbfgs g.g");
+    TT_CUDA(cudaMemcpyAsync(st->pinned, st->dots, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy");
+    TT_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    st->G(st->ig(), st->ig()) = st->pinned[0];
+    return TT_OK;
+}
+
 extern "C" {
 
 tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0, const void *I, const void *W, tt_lbfgs **out)
 {
     if (!out) { set_error("tt_lbfgs_create: out must not be NULL"); return TT_INVALID_ARG; }
     *out = nullptr;
-    if (!h || !c0 || !I || m < 1 || m > 64) {
+    if (!h || !c0 || !I || m < 1 || m > kMaxM) {
         set_error("tt_lbfgs_create: need a handle, c0, I and 1 <= m <= 64");
         return TT_INVALID_ARG;
     }
     tt_lbfgs *st = new tt_lbfgs();
     st->h = h;
     st->m = m;
+    st->nb = 2 * m + 1;
+    st->gram.assign((size_t)st->nb * st->nb, 0.0);
     st->n = h->nvox() * h->K;
     st->I = I;
     st->W = W;
     const size_t bytes = h->esize() * st->n;
+    const size_t pitch = (bytes + 255) / 256 * 256;     // 256-byte aligned vectors in one slab
+    cudaError_t e = cudaMalloc(&st->slab, pitch * (7 + 2 * (size_t)m));
+    if (e != cudaSuccess) { free_state(st); return cuda_fail(e, "tt_lbfgs_create: cudaMalloc"); }
+    char *base = (char *)st->slab;
     void **bufs[] = {&st->x, &st->g, &st->d, &st->xt, &st->gt, &st->ss, &st->ys};
-    for (void **b : bufs) {
-        cudaError_t e = cudaMalloc(b, bytes);
-        if (e != cudaSuccess) { free_state(st); return cuda_fail(e, "tt_lbfgs_create: cudaMalloc"); }
-    }
+    for (void **b : bufs) { *b = base; base += pitch; }
     st->S.assign(m, nullptr);
     st->Y.assign(m, nullptr);
     for (int i = 0; i < m; ++i) {
-        cudaError_t e = cudaMalloc(&st->S[i], bytes);
-        if (e == cudaSuccess) e = cudaMalloc(&st->Y[i], bytes);
-        if (e != cudaSuccess) { free_state(st); return cuda_fail(e, "tt_lbfgs_create: cudaMalloc"); }
+        st->S[i] = base; base += pitch;
+        st->Y[i] = base; base += pitch;
     }
-    st->rho.assign(m, 0.0);
-    st->sy.assign(m, 0.0);
-    st->yy.assign(m, 0.0);
-    cudaError_t e = cudaMalloc(&st->scal, sizeof(double) * (2 * m + 8));
-    if (e == cudaSuccess) e = cudaMalloc(&st->partials, sizeof(double) * kDotBlocks);
-    if (e == cudaSuccess) e = cudaMallocHost(&st->pinned, sizeof(double) * 8);
+    const size_t rows = 6 + 6 * (size_t)m;
+    e = cudaMalloc(&st->part, sizeof(double) * std::max<size_t>(rows * kPairBlocks, kDotBlocks));
+    if (e == cudaSuccess) e = cudaMalloc(&st->dots, sizeof(double) * rows);
+    if (e == cudaSuccess) e = cudaMallocHost(&st->pinned, sizeof(double) * rows);
     if (e == cudaSuccess) e = cudaMemcpyAsync(st->x, c0, bytes, cudaMemcpyDeviceToDevice, h->stream);
     if (e != cudaSuccess) { free_state(st); return cuda_fail(e, "tt_lbfgs_create"); }
     tt_status s = (h->prec != TT_F64)
@@ -205,6 +461,7 @@ tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0, const void *I, co
                       : tt_grad_enqueue<double>(h, (const double *)st->x, (const double *)I, (const double *)W,
                                                 (double *)st->g);
     if (s == TT_OK) s = tt_read_loss(h, &st->f);
+    if (s == TT_OK) s = (h->prec != TT_F64) ? initial_gram<float>(st) : initial_gram<double>(st);
     if (s != TT_OK) { free_state(st); return s; }
     *out = st;
     return TT_OK;

@@ -13,12 +13,15 @@ __global__ void k_l2(const T *__restrict__ c, long long n, T *__restrict__ grad,
 {
     __shared__ double red[32];
     double v = 0.0;
+    Dot2 a = {0.f, 0.f};           // float: compensated FP32 per thread, FP64 across threads
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {
         const T x = c[t];
-        v = fma((double)x, (double)x, v);
+        if constexpr (std::is_same<T, float>::value) dot2_add(a, x, x);
+        else v = fma(x, x, v);
         if (grad) grad[t] = T(2) * x;
     }
+    if constexpr (std::is_same<T, float>::value) v = dot2_value(a);
     v = block_sum(v, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = v;
 }

@@ -44,6 +44,21 @@ def test_regularisers_match_oracle(prec, tol, delta):
     assert dt == g.dtype
 
 
+def test_fp32_sum_of_squares_is_accurate_to_double_rounding():
+    """FP32 vectors are reduced with compensated FP32 products and sums per
+    thread (Ogita-Rump-Oishi Dot2) and FP64 across threads: the sum of
+    squares of a full-size FP32 volume matches the FP64 sum of the same
+    float values to 1e-12, far below FP32 rounding."""
+    st = synth.workload("ell64")
+    h = tt.Handle(st, "f32")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    c = torch.randn(st.volume_shape, device="cuda", generator=gen) * 3.0 + 0.7
+    v, _ = h.l2_norm(c, want_grad=False)
+    ref = float(np.sum(c.cpu().numpy().astype(np.float64) ** 2))
+    assert abs(v - ref) <= 1e-12 * ref
+
+
 def _crop_setup(n=12, n_proj=6, ell_max=6):
     full = synth.workload("ply100")
     idx = np.linspace(0, full.S - 1, n_proj).round().astype(int)
