@@ -194,8 +194,11 @@ tt_status tt_tv_huber_f64(tt_handle *h, const double *c_dev, double delta, doubl
  * m and backtracking Armijo line search (c1 = 1e-4, step halving, at most 20
  * evaluations per iteration; first iteration steps 1/|g| along -g; a pair is
  * stored only if s.y > 1e-10 |s||y|; a non-descent direction clears the
- * memory).  Vectors live on the device in the handle's precision; every dot
- * product is accumulated in FP64.  I_dev / W_dev (W may be NULL) are
+ * memory).  Vectors live on the device in the handle's precision.  The
+ * two loops run on the FP64 Gram matrix of the stored pairs and the gradient
+ * (the same recursion in exact arithmetic; three vector kernels per
+ * iteration); dot products of float vectors use compensated FP32 (Dot2)
+ * accumulation per thread and FP64 across threads.  I_dev / W_dev (W may be NULL) are
  * referenced, not copied: keep them alive and unchanged while the state
  * exists.  tt_lbfgs_create evaluates the loss and gradient at c0_dev. */
 tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0_dev, const void *I_dev,
