@@ -297,6 +297,15 @@ tt_status tt_conv3d_bf16(int nx, int ny, int nz, int cin, int cout, const void *
 tt_status tt_conv3d_wgrad_bf16(int nx, int ny, int nz, int cin, int cout, const void *x_dev, const void *dy_dev,
                                float *dw_dev, void *stream);
 
+/* One 128 x N tile on the tcgen05 tensor cores (the building block of the
+ * warm start's convolutions; the paper has no counterpart): C = A B^T with
+ * A_dev [128][K] and B_dev [N][K] bfloat16 row-major, C_dev [128][N] float,
+ * all device memory.  N and K multiples of 16 in [16, 256].  One CTA on
+ * stream; *status_dev (device int) is set to 0, or to 1 when the wait for
+ * the tensor cores gave up (results then unset). */
+tt_status tt_umma_gemm_bf16(const void *A_dev, const void *B_dev, float *C_dev, int N, int K, int *status_dev,
+                            void *stream);
+
 /* Phantom helper: SH coefficients of zonal functions rotated to unit axes n,
  * c_lm = a_l sqrt(4 pi/(2l+1)) Y_lm(n) (addition theorem).  dirs_dev [n][3],
  * amps_dev [n][ell_max/2+1], c_dev [n][K], FP32, device, on stream. */

@@ -104,6 +104,7 @@ SIGNATURES = {
     "tt_wsnet_get_weights": (ctypes.c_int, [_P, _P]),
     "tt_conv3d_bf16": (ctypes.c_int, [ctypes.c_int] * 5 + [_P, _P, ctypes.c_int, _P, _P]),
     "tt_conv3d_wgrad_bf16": (ctypes.c_int, [ctypes.c_int] * 5 + [_P, _P, _P, _P]),
+    "tt_umma_gemm_bf16": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "tt_zonal_to_sh": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, _P, _P, _P, _P]),
     "tt_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "tt_profile_read": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_longlong)]),
@@ -421,6 +422,23 @@ class MITRA:
             self.close()
         except Exception:
             pass
+
+
+def umma_gemm_bf16(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
+    """C = A B^T for A [128][K], B [N][K] bfloat16 on the tcgen05 tensor cores
+    (one tile); raises if the kernel's wait for the tensor cores gave up."""
+    lib = load()
+    N, K = B.shape
+    A = A.contiguous()
+    B = B.contiguous()
+    C = torch.empty((128, N), dtype=torch.float32, device=A.device)
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib.tt_umma_gemm_bf16(_dptr(A, torch.bfloat16, (128, K), "A"), _dptr(B, torch.bfloat16, (N, K), "B"),
+                                 ctypes.c_void_p(C.data_ptr()), int(N), int(K), ctypes.c_void_p(status.data_ptr()),
+                                 _stream_ptr()), "tt_umma_gemm_bf16")
+    if int(status.item()) != 0:
+        raise TTError(TT_CUDA_ERROR, "tt_umma_gemm_bf16", "tensor-core wait gave up")
+    return C
 
 
 def zonal_to_sh(ell_max: int, dirs: torch.Tensor, amps: torch.Tensor) -> torch.Tensor:

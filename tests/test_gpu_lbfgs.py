@@ -42,6 +42,24 @@ def test_lbfgs_fp64_matches_oracle_step_by_step():
     assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
 
 
+@pytest.mark.parametrize("m", [1, 3])
+def test_lbfgs_fp64_short_memory_wraps_like_the_oracle(m):
+    """With m = 1 or 3 the pair store wraps around within a few iterations:
+    the Gram matrix rows of the replaced pair must be rebuilt exactly."""
+    st, g, I = _problem(5, n=(7, 8, 6))
+    B = oracle.basis_matrix(g)
+    fg = lambda x: oracle.gradient_residual(g, x.reshape(st.volume_shape), I, None, B)
+    ref = OracleLBFGS(fg, np.zeros(int(np.prod(st.volume_shape))), m=m)
+    h = tt.Handle(st, "f64")
+    opt = tt.LBFGS(h, torch.zeros(st.volume_shape, dtype=torch.float64, device="cuda"),
+                   torch.as_tensor(I, device="cuda"), None, m=m)
+    for it in range(12):
+        f_ref, ne_ref, st_ref = ref.step()
+        f, ne, status = opt.step()
+        assert status == st_ref == 0 and ne == ne_ref, it
+        assert abs(f - f_ref) <= 1e-9 * f_ref, (it, f, f_ref)
+
+
 def test_lbfgs_fp32_tracks_oracle_and_decreases():
     st, g, I = _problem(3, n=(10, 9, 8), ell_max=4)
     B = oracle.basis_matrix(g)
