@@ -1,6 +1,8 @@
 // tt_conv.cu -- 3x3x3 convolutions of the learned warm start on the tensor
-// cores (bfloat16 inputs, float accumulation, mma.sync m16n8k16) and the
-// small kernels of its training step (ReLU mask, squared error, Adam).
+// cores (bfloat16 inputs, float accumulation): the forward convolution (and
+// with flipped weights the data gradient) on tcgen05 with tensor-memory
+// accumulators, the weight gradient with mma.sync m16n8k16; and the small
+// kernels of the training step (ReLU mask, squared error, Adam).
 //
 // Layouts: activations a[v][C] bfloat16, v = (x*ny + y)*nz + z, C in {16, 32}
 // (channels zero padded); convolution weights wk[t][Cout][Cin] bfloat16, t =
@@ -14,6 +16,7 @@
 #include <vector>
 
 #include "tt_internal.cuh"
+#include "tt_umma.cuh"
 
 namespace tt {
 
@@ -44,109 +47,157 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// ------------------------------------------------------------ forward conv
+// ------------------------------------------------ forward conv, tcgen05
 //
-// CTA tile: 2 (x) x 4 (y) x 32 (z) output voxels; warp w owns the 32-voxel z
-// row (x0 + w/4, y0 + w%4) as two m16 tiles.  The input brick with its
-// one-voxel halo (4 x 6 x 34 voxels) and all 27 weight matrices are staged in
-// shared memory (rows padded by 16 bytes so that ldmatrix is bank-conflict
-// free); the K loop runs over the 27 taps x CIN/16 channel chunks.
-constexpr int kCX = 2, kCY = 4, kCZ = 32;
-constexpr int kBX = kCX + 2, kBY = kCY + 2, kBZ = kCZ + 2;
+// Implicit GEMM on the fifth-generation tensor cores: a tile is M = 128
+// output voxels (one x, four y rows of 32 z), N = COUT, K = 27 taps x CIN.
+// For tap (dx, dy, dz) the A operand is the input shifted by the tap; with
+// the tile's rows stored 16 bytes apart (row m = 32 y + z), a shift in y or x
+// is a change of the descriptor's start address, so the input is staged
+// once per z shift: three copies [dz][CIN/8][x 3][y 6][z 32] of 16-byte
+// (8-channel) chunks, zeros outside the volume.  Core matrices: SBO = 128 B
+// (next 8 rows), LBO = 3 * 6 * 512 B (next 8 channels).  The weights are
+// staged once per CTA as [tap][CIN/8][COUT][8] (SBO = 128 B, LBO = COUT * 16
+// B).  One thread issues the 27 * CIN / 16 MMAs (M 128, N COUT, K 16) into
+// COUT tensor-memory columns, commits to an mbarrier, and the four warps read
+// their 32 rows back (ReLU, bf16 or f32 store).  Persistent CTAs loop over
+// tiles.  A wait that gives up writes NaN into the tile, which every
+// consumer of the output sees.
+constexpr uint32_t kTcWaitTries = 1u << 22;
+constexpr int kTcThreads = 256;
 
 template <int CIN, int COUT>
-constexpr size_t conv_fwd_smem()
-{
-    return (size_t)(kBX * kBY * kBZ * (CIN + 8) + 27 * COUT * (CIN + 8)) * 2;
-}
+struct TcConvSmem {
+    static constexpr uint32_t copy = (CIN / 8) * 3 * 6 * 512;   // one z-shifted input copy
+    static constexpr uint32_t tap = COUT * CIN * 2;              // one tap's weights
+    static constexpr uint32_t wts = 3 * copy;
+    static constexpr uint32_t mbar = wts + 27 * tap;
+    static constexpr uint32_t bytes = mbar + 16;
+};
 
 template <int CIN, int COUT, bool RELU, bool OUT_F32>
-__global__ void __launch_bounds__(256)
-k_conv3d_fwd(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ wk, void *__restrict__ out,
-             int nx, int ny, int nz, int ty, int tz)
+__global__ void __launch_bounds__(kTcThreads)
+k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ wk, void *__restrict__ out,
+                int nx, int ny, int nz, int tiles_y, int tiles_z, int n_tiles)
 {
-    constexpr int RS = CIN + 8;     // padded row stride (elements)
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __nv_bfloat16 *brick = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
-    __nv_bfloat16 *ws = brick + kBX * kBY * kBZ * RS;
+    using L = TcConvSmem<CIN, COUT>;
+    constexpr int KC = CIN / 8;
+    constexpr uint32_t kLboA = 3 * 6 * 512, kLboB = COUT * 16;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L::mbar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    const int b = blockIdx.x;
-    const int bz = b % tz, by = (b / tz) % ty, bx = b / (tz * ty);
-    const int x0 = bx * kCX, y0 = by * kCY, z0 = bz * kCZ;
-
-    // stage the input brick (zeros outside the volume) and the weights
-    constexpr int CH = CIN / 8;     // 16-byte chunks per row
-    for (int t = threadIdx.x; t < kBX * kBY * kBZ * CH; t += blockDim.x) {
-        const int c = t % CH, r = t / CH;
-        const int iz = r % kBZ, iy = (r / kBZ) % kBY, ix = r / (kBZ * kBY);
-        const int gx = x0 - 1 + ix, gy = y0 - 1 + iy, gz = z0 - 1 + iz;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if ((unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz)
-            v = __ldg(reinterpret_cast<const uint4 *>(in + (((long long)gx * ny + gy) * nz + gz) * CIN) + c);
-        *reinterpret_cast<uint4 *>(brick + r * RS + c * 8) = v;
+    if (warp == 0) umma::tmem_alloc(tslot, 32);
+    if (tid == 0) umma::mbar_init(mbar, 1);
+    for (int e = tid; e < 27 * COUT * KC; e += blockDim.x) {          // weights [t][co][ci] -> [t][ci/8][co][8]
+        const int kc = e % KC, co = (e / KC) % COUT, t = e / (KC * COUT);
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(wk + ((size_t)t * COUT + co) * CIN) + kc);
+        *reinterpret_cast<uint4 *>(smem + L::wts + t * L::tap + kc * kLboB + co * 16) = v;
     }
-    for (int t = threadIdx.x; t < 27 * COUT * CH; t += blockDim.x) {
-        const int c = t % CH, r = t / CH;
-        *reinterpret_cast<uint4 *>(ws + r * RS + c * 8) = __ldg(reinterpret_cast<const uint4 *>(wk + r * CIN) + c);
-    }
+    umma::fence_before_sync();
     __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = umma::idesc_bf16_f32(128, COUT);
+    const uint32_t s_act = umma::smem_u32(smem), s_wts = umma::smem_u32(smem + L::wts);
+    uint32_t parity = 0;
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int xl = warp / kCY, yl = warp % kCY;
-    constexpr int NT = COUT / 8;
-    float acc[2][NT][4];
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int tz = tile % tiles_z, ty = (tile / tiles_z) % tiles_y, x0 = tile / (tiles_z * tiles_y);
+        const int y0 = ty * 4, z0 = tz * 32;
+        // Each input chunk (voxel x0-1+xh, y0-1+yh, z0-1+e, channels 8 kc..)
+        // is loaded once, all of a thread's loads in flight together, and
+        // stored into the copies d that use it (z slot e - d).
+        constexpr int kChunks = 3 * 6 * 34 * KC, kPer = (kChunks + kTcThreads - 1) / kTcThreads;
+        uint4 val[kPer];
 #pragma unroll
-    for (int m = 0; m < 2; ++m)
+        for (int j = 0; j < kPer; ++j) {
+            const int e = tid + j * kTcThreads;
+            val[j] = make_uint4(0, 0, 0, 0);
+            if (e < kChunks) {
+                const int ez = e % 34, kc = (e / 34) % KC, yh = (e / (34 * KC)) % 6, xh = e / (34 * KC * 6);
+                const int gx = x0 - 1 + xh, gy = y0 - 1 + yh, gz = z0 - 1 + ez;
+                if ((unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz)
+                    val[j] = __ldg(reinterpret_cast<const uint4 *>(in + (((size_t)gx * ny + gy) * nz + gz) * CIN) + kc);
+            }
+        }
 #pragma unroll
-        for (int n = 0; n < NT; ++n)
+        for (int j = 0; j < kPer; ++j) {
+            const int e = tid + j * kTcThreads;
+            if (e < kChunks) {
+                const int ez = e % 34, kc = (e / 34) % KC, yh = (e / (34 * KC)) % 6, xh = e / (34 * KC * 6);
+                uint8_t *row = smem + ((kc * 3 + xh) * 6 + yh) * 512;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[m][n][i] = 0.f;
-
-    for (int t = 0; t < 27; ++t) {
-        const int dx = t / 9 - 1, dy = (t / 3) % 3 - 1, dz = t % 3 - 1;
-        const int rowbase = ((xl + 1 + dx) * kBY + (yl + 1 + dy)) * kBZ + 1 + dz;
-#pragma unroll
-        for (int c0 = 0; c0 < CIN; c0 += 16) {
-            unsigned a[2][4];
-#pragma unroll
-            for (int m = 0; m < 2; ++m)
-                ldsm_x4(a[m], brick + (rowbase + 16 * m + (lane & 15)) * RS + c0 + (lane >> 4) * 8);
-#pragma unroll
-            for (int np = 0; np < NT / 2; ++np) {
-                unsigned bb[4];
-                ldsm_x4(bb, ws + (t * COUT + np * 16 + (lane >> 4) * 8 + (lane & 7)) * RS + c0 + ((lane >> 3) & 1) * 8);
-#pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    mma_bf16(acc[m][2 * np], a[m], bb[0], bb[1]);
-                    mma_bf16(acc[m][2 * np + 1], a[m], bb[2], bb[3]);
+                for (int d = 0; d < 3; ++d) {
+                    const int zl = ez - d;
+                    if (zl >= 0 && zl < 32) *reinterpret_cast<uint4 *>(row + d * L::copy + zl * 16) = val[j];
                 }
             }
         }
+        umma::fence_async_smem();
+        umma::fence_before_sync();
+        __syncthreads();
+        umma::fence_after_sync();
+        if (tid == 0) {
+            for (int t = 0; t < 27; ++t) {
+                const int dx = t / 9, dy = (t / 3) % 3, dz = t % 3;       // tap offset + 1
+                const uint32_t a0 = s_act + dz * L::copy + (dx * 6 + dy) * 512;
+                const uint32_t b0 = s_wts + t * L::tap;
+#pragma unroll
+                for (int kk = 0; kk < CIN / 16; ++kk)
+                    umma::mma_bf16(tmem, umma::smem_desc(a0 + kk * 2 * kLboA, kLboA, 128),
+                                   umma::smem_desc(b0 + kk * 2 * kLboB, kLboB, 128), idesc, (t | kk) ? 1u : 0u);
+            }
+            umma::mma_commit(mbar);
+        }
+        const bool ok = umma::mbar_wait(mbar, parity, kTcWaitTries);
+        parity ^= 1u;
+        umma::fence_after_sync();
+        // warp w reads tensor-memory lanes 32 (w % 4) .. (rows: y0 + w % 4,
+        // z0 + lane), columns [16 (w / 4), 16 (w / 4) + 16) when COUT = 32
+        constexpr int CW = COUT / (kTcThreads / 128);               // columns per warp
+        const int quad = warp & 3, c_base = (warp >> 2) * CW;
+        static_assert(CW == 8 || CW == 16, "a warp reads 8 or 16 accumulator columns");
+        float v[CW];
+        if constexpr (CW == 16) umma::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c_base, v);
+        else umma::tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c_base, v);
+        if (!ok) {
+#pragma unroll
+            for (int i = 0; i < CW; ++i) v[i] = __int_as_float(0x7fc00000);
+        }
+        const int gy = y0 + quad, gz = z0 + lane;
+        if (gy < ny && gz < nz) {
+            const size_t vox = ((size_t)x0 * ny + gy) * nz + gz;
+            if constexpr (OUT_F32) {
+                float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + vox * COUT + c_base);
+#pragma unroll
+                for (int i = 0; i < CW / 4; ++i) {
+                    float4 q = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    if (RELU) { q.x = fmaxf(q.x, 0.f); q.y = fmaxf(q.y, 0.f); q.z = fmaxf(q.z, 0.f); q.w = fmaxf(q.w, 0.f); }
+                    o[i] = q;
+                }
+            } else {
+                uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + vox * COUT + c_base);
+#pragma unroll
+                for (int i = 0; i < CW / 8; ++i) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float a = v[8 * i + 2 * j], b = v[8 * i + 2 * j + 1];
+                        if (RELU) { a = fmaxf(a, 0.f); b = fmaxf(b, 0.f); }
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
+                        w[j] = *reinterpret_cast<const uint32_t *>(&h2);
+                    }
+                    o[i] = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+        }
+        umma::fence_before_sync();
+        __syncthreads();                       // tensor memory and staged input free for the next tile
+        umma::fence_after_sync();
     }
-
-    const int gx = x0 + xl, gy = y0 + yl;
-    if (gx >= nx || gy >= ny) return;
-    const int g = lane >> 2, tig = lane & 3;
-#pragma unroll
-    for (int m = 0; m < 2; ++m)
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int gz = z0 + 16 * m + g + 8 * half;
-            if (gz >= nz) continue;
-            const long long v = ((long long)gx * ny + gy) * nz + gz;
-#pragma unroll
-            for (int n = 0; n < NT; ++n) {
-                float e0 = acc[m][n][2 * half], e1 = acc[m][n][2 * half + 1];
-                if (RELU) { e0 = fmaxf(e0, 0.f); e1 = fmaxf(e1, 0.f); }
-                const int co = n * 8 + 2 * tig;
-                if (OUT_F32) {
-                    *reinterpret_cast<float2 *>(static_cast<float *>(out) + v * COUT + co) = make_float2(e0, e1);
-                } else {
-                    *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(out) + v * COUT + co) =
-                        __floats2bfloat162_rn(e0, e1);
-                }
-            }
-        }
+    if (warp == 0) umma::tmem_dealloc(tmem, 32);
 }
 
 // ------------------------------------------------------- weight gradient
@@ -333,20 +384,36 @@ static unsigned grid_n(long long n)
     return (unsigned)(b < 1 ? 1 : (b > 152LL * 16 ? 152LL * 16 : b));
 }
 
-// Launches the forward convolution for a (CIN, COUT) pair.
+static int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n < 1) n = 1;
+    }
+    return n;
+}
+
+// Launches the forward convolution (tcgen05 kernel) for a (CIN, COUT) pair:
+// persistent CTAs, as many per SM as the staged input and weights allow.
 cudaError_t conv3d_forward(const __nv_bfloat16 *in, const __nv_bfloat16 *wk, void *out, int nx, int ny, int nz, int cin,
                            int cout, bool relu, bool out_f32, cudaStream_t st)
 {
-    const int tx = (nx + kCX - 1) / kCX, ty = (ny + kCY - 1) / kCY, tz = (nz + kCZ - 1) / kCZ;
-    const unsigned grid = (unsigned)(tx * ty * tz);
+    const int tiles_y = (ny + 3) / 4, tiles_z = (nz + 31) / 32;
+    const int n_tiles = nx * tiles_y * tiles_z;
 #define TT_CONV_LAUNCH(CI, CO, R, F)                                                                  \
     do {                                                                                              \
-        auto kern = k_conv3d_fwd<CI, CO, R, F>;                                                       \
-        constexpr size_t sm = conv_fwd_smem<CI, CO>();                                                \
+        auto kern = k_conv3d_fwd_tc<CI, CO, R, F>;                                                    \
+        constexpr uint32_t sm = TcConvSmem<CI, CO>::bytes;                                            \
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);             \
-        kern<<<grid, 256, sm, st>>>(in, wk, out, nx, ny, nz, ty, tz);                                 \
+        const int per_sm = sm <= 110u * 1024u ? 2 : 1;                                                \
+        const int grid = n_tiles < sm_count() * per_sm ? n_tiles : sm_count() * per_sm;              \
+        kern<<<grid, kTcThreads, sm, st>>>(in, wk, out, nx, ny, nz, tiles_y, tiles_z, n_tiles);       \
         return cudaGetLastError();                                                                    \
     } while (0)
+    if (n_tiles < 1) return cudaSuccess;
     if (cin == 16 && cout == 32 && relu && !out_f32) TT_CONV_LAUNCH(16, 32, true, false);
     if (cin == 32 && cout == 32 && relu && !out_f32) TT_CONV_LAUNCH(32, 32, true, false);
     if (cin == 32 && cout == 16 && !relu && out_f32) TT_CONV_LAUNCH(32, 16, false, true);
