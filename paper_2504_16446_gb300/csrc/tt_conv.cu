@@ -50,47 +50,139 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
 // ------------------------------------------------ forward conv, tcgen05
 //
 // Implicit GEMM on the fifth-generation tensor cores: a tile is M = 128
-// output voxels (one x, four y rows of 32 z), N = COUT, K = 27 taps x CIN.
-// For tap (dx, dy, dz) the A operand is the input shifted by the tap; with
-// the tile's rows stored 16 bytes apart (row m = 32 y + z), a shift in y or x
-// is a change of the descriptor's start address, so the input is staged
-// once per z shift: three copies [dz][CIN/8][x 3][y 6][z 32] of 16-byte
-// (8-channel) chunks, zeros outside the volume.  Core matrices: SBO = 128 B
-// (next 8 rows), LBO = 3 * 6 * 512 B (next 8 channels).  The weights are
-// staged once per CTA as [tap][CIN/8][COUT][8] (SBO = 128 B, LBO = COUT * 16
-// B).  One thread issues the 27 * CIN / 16 MMAs (M 128, N COUT, K 16) into
-// COUT tensor-memory columns, commits to an mbarrier, and the four warps read
-// their 32 rows back (ReLU, bf16 or f32 store).  Persistent CTAs loop over
-// tiles.  A wait that gives up writes NaN into the tile, which every
-// consumer of the output sees.
+// output voxels (one x plane, four y rows of 32 z), N = COUT, K = 27 taps x
+// CIN.  For tap (dx, dy, dz) the A operand is the input shifted by the tap.
+// The tile's rows are 16 bytes apart (row m = 32 y + z), so a shift in y is
+// a change of the descriptor's start address (512 B per y row) and a shift
+// in x selects another staged plane; a shift in z would cross the ends of
+// the 32-voxel rows, so every plane is staged once per z shift: a plane
+// buffer is [dz 3][CIN/8][y 6][z 32] 16-byte (8-channel) chunks, zeros
+// outside the volume.  Core matrices: SBO = 128 B (next 8 rows), LBO = 6 *
+// 512 B (next 8 channels).  Weights are staged once per CTA as
+// [tap][CIN/8][COUT][8] (SBO = 128 B, LBO = COUT * 16 B).
+//
+// Pipeline.  A persistent CTA walks runs of kSegX consecutive x planes of one
+// (y, z) tile column.  Tile x needs planes x-1, x, x+1 from a ring of four
+// plane buffers, so each step stages one new plane.  Step for tile x: one
+// thread issues its 27 * CIN / 16 MMAs (M 128, N COUT, K 16) into
+// tensor-memory accumulator x % 2 and commits them to mbarrier x % 2; while
+// they run, all eight warps wait for tile x-1's mbarrier, write tile x-1 out
+// from its accumulator (ReLU, bf16 or f32), and stage plane x+2 into the
+// buffer that tile x-1 was the last to read.  A wait that gives up writes
+// NaN into its tile, which every consumer of the output sees.
 constexpr uint32_t kTcWaitTries = 1u << 22;
 constexpr int kTcThreads = 256;
+constexpr int kSegX = 16;
 
 template <int CIN, int COUT>
 struct TcConvSmem {
-    static constexpr uint32_t copy = (CIN / 8) * 3 * 6 * 512;   // one z-shifted input copy
-    static constexpr uint32_t tap = COUT * CIN * 2;              // one tap's weights
-    static constexpr uint32_t wts = 3 * copy;
+    static constexpr uint32_t copy = (CIN / 8) * 6 * 512;     // one z-shifted copy of a plane
+    static constexpr uint32_t plane = 3 * copy;
+    static constexpr uint32_t tap = COUT * CIN * 2;            // one tap's weights
+    static constexpr uint32_t wts = 4 * plane;
     static constexpr uint32_t mbar = wts + 27 * tap;
-    static constexpr uint32_t bytes = mbar + 16;
+    static constexpr uint32_t bytes = mbar + 32;
 };
+
+// Stages input plane gx (zeros outside the volume) into plane buffer `buf`:
+// each input chunk (y0-1+yh, z0-1+ez, channels 8 kc..) is loaded once, all of
+// a thread's loads in flight together, and stored into the copies d that use
+// it (z slot ez - d).
+template <int CIN>
+__device__ __forceinline__ void stage_plane(uint8_t *buf, const __nv_bfloat16 *__restrict__ in, int gx, int y0,
+                                            int z0, int nx, int ny, int nz, int tid)
+{
+    constexpr int KC = CIN / 8, kChunks = 6 * 34 * KC, kPer = (kChunks + kTcThreads - 1) / kTcThreads;
+    constexpr uint32_t copy = KC * 6 * 512;
+    uint4 val[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int e = tid + j * kTcThreads;
+        val[j] = make_uint4(0, 0, 0, 0);
+        if (e < kChunks) {
+            const int ez = e % 34, kc = (e / 34) % KC, yh = e / (34 * KC);
+            const int gy = y0 - 1 + yh, gz = z0 - 1 + ez;
+            if ((unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz)
+                val[j] = __ldg(reinterpret_cast<const uint4 *>(in + (((size_t)gx * ny + gy) * nz + gz) * CIN) + kc);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int e = tid + j * kTcThreads;
+        if (e < kChunks) {
+            const int ez = e % 34, kc = (e / 34) % KC, yh = e / (34 * KC);
+            uint8_t *row = buf + (kc * 6 + yh) * 512;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int zl = ez - d;
+                if (zl >= 0 && zl < 32) *reinterpret_cast<uint4 *>(row + d * copy + zl * 16) = val[j];
+            }
+        }
+    }
+}
+
+// Tile epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. (rows y0 +
+// w % 4, z0 + lane) and the w / 4-th half of the COUT columns of accumulator
+// `acc_col`.
+template <int COUT, bool RELU, bool OUT_F32>
+__device__ __forceinline__ void tile_epilogue(uint32_t tmem, uint32_t acc_col, bool ok, void *__restrict__ out, int x0,
+                                              int y0, int z0, int ny, int nz, int warp, int lane)
+{
+    constexpr int CW = COUT / (kTcThreads / 128);
+    static_assert(CW == 8 || CW == 16, "a warp reads 8 or 16 accumulator columns");
+    const int quad = warp & 3, c_base = (warp >> 2) * CW;
+    float v[CW];
+    const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + acc_col + (uint32_t)c_base;
+    if constexpr (CW == 16) umma::tmem_ld16(taddr, v);
+    else umma::tmem_ld8(taddr, v);
+    if (!ok) {
+#pragma unroll
+        for (int i = 0; i < CW; ++i) v[i] = __int_as_float(0x7fc00000);
+    }
+    const int gy = y0 + quad, gz = z0 + lane;
+    if (gy >= ny || gz >= nz) return;
+    const size_t vox = ((size_t)x0 * ny + gy) * nz + gz;
+    if constexpr (OUT_F32) {
+        float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + vox * COUT + c_base);
+#pragma unroll
+        for (int i = 0; i < CW / 4; ++i) {
+            float4 q = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            if (RELU) { q.x = fmaxf(q.x, 0.f); q.y = fmaxf(q.y, 0.f); q.z = fmaxf(q.z, 0.f); q.w = fmaxf(q.w, 0.f); }
+            o[i] = q;
+        }
+    } else {
+        uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + vox * COUT + c_base);
+#pragma unroll
+        for (int i = 0; i < CW / 8; ++i) {
+            uint32_t w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float a = v[8 * i + 2 * j], b = v[8 * i + 2 * j + 1];
+                if (RELU) { a = fmaxf(a, 0.f); b = fmaxf(b, 0.f); }
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
+                w[j] = *reinterpret_cast<const uint32_t *>(&h2);
+            }
+            o[i] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
 
 template <int CIN, int COUT, bool RELU, bool OUT_F32>
 __global__ void __launch_bounds__(kTcThreads)
 k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ wk, void *__restrict__ out,
-                int nx, int ny, int nz, int tiles_y, int tiles_z, int n_tiles)
+                int nx, int ny, int nz, int tiles_y, int tiles_z, int segs_x, int n_units)
 {
     using L = TcConvSmem<CIN, COUT>;
     constexpr int KC = CIN / 8;
-    constexpr uint32_t kLboA = 3 * 6 * 512, kLboB = COUT * 16;
+    constexpr uint32_t kLboA = 6 * 512, kLboB = COUT * 16;
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L::mbar);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L::mbar);   // [2]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    if (warp == 0) umma::tmem_alloc(tslot, 32);
-    if (tid == 0) umma::mbar_init(mbar, 1);
-    for (int e = tid; e < 27 * COUT * KC; e += blockDim.x) {          // weights [t][co][ci] -> [t][ci/8][co][8]
+    if (warp == 0) umma::tmem_alloc(tslot, 2 * 32);
+    if (tid == 0) { umma::mbar_init(mbar, 1); umma::mbar_init(mbar + 1, 1); }
+    for (int e = tid; e < 27 * COUT * KC; e += kTcThreads) {          // weights [t][co][ci] -> [t][ci/8][co][8]
         const int kc = e % KC, co = (e / KC) % COUT, t = e / (KC * COUT);
         const uint4 v = __ldg(reinterpret_cast<const uint4 *>(wk + ((size_t)t * COUT + co) * CIN) + kc);
         *reinterpret_cast<uint4 *>(smem + L::wts + t * L::tap + kc * kLboB + co * 16) = v;
@@ -100,104 +192,54 @@ k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__res
     umma::fence_after_sync();
     const uint32_t tmem = *tslot;
     const uint32_t idesc = umma::idesc_bf16_f32(128, COUT);
-    const uint32_t s_act = umma::smem_u32(smem), s_wts = umma::smem_u32(smem + L::wts);
-    uint32_t parity = 0;
+    const uint32_t s_planes = umma::smem_u32(smem), s_wts = umma::smem_u32(smem + L::wts);
+    uint32_t issued[2] = {0, 0};          // tiles committed per mbarrier (phase of the next wait)
 
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int tz = tile % tiles_z, ty = (tile / tiles_z) % tiles_y, x0 = tile / (tiles_z * tiles_y);
-        const int y0 = ty * 4, z0 = tz * 32;
-        // Each input chunk (voxel x0-1+xh, y0-1+yh, z0-1+e, channels 8 kc..)
-        // is loaded once, all of a thread's loads in flight together, and
-        // stored into the copies d that use it (z slot e - d).
-        constexpr int kChunks = 3 * 6 * 34 * KC, kPer = (kChunks + kTcThreads - 1) / kTcThreads;
-        uint4 val[kPer];
+    for (int unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
+        const int sx = unit % segs_x, tz = (unit / segs_x) % tiles_z, ty = unit / (segs_x * tiles_z);
+        const int y0 = ty * 4, z0 = tz * 32, xa = sx * kSegX;
+        const int xb = min(nx, xa + kSegX);
+        // planes xa-1, xa, xa+1 before the first tile (the ring is idle here)
+        for (int px = xa - 1; px <= xa + 1; ++px)
+            stage_plane<CIN>(smem + (px & 3) * L::plane, in, px, y0, z0, nx, ny, nz, tid);
+        for (int x = xa; x <= xb; ++x) {
+            const int i = x - xa;                 // step: tile x issued, tile x-1 written out, plane x+2 staged
+            umma::fence_async_smem();
+            umma::fence_before_sync();
+            __syncthreads();
+            umma::fence_after_sync();
+            if (x < xb && tid == 0) {
+                const uint32_t acc = tmem + (uint32_t)(32 * (i & 1));
+                for (int t = 0; t < 27; ++t) {
+                    const int dx = t / 9, dy = (t / 3) % 3, dz = t % 3;   // tap offset + 1
+                    const uint32_t a0 = s_planes + ((x - 1 + dx) & 3) * L::plane + dz * L::copy + dy * 512;
+                    const uint32_t b0 = s_wts + t * L::tap;
 #pragma unroll
-        for (int j = 0; j < kPer; ++j) {
-            const int e = tid + j * kTcThreads;
-            val[j] = make_uint4(0, 0, 0, 0);
-            if (e < kChunks) {
-                const int ez = e % 34, kc = (e / 34) % KC, yh = (e / (34 * KC)) % 6, xh = e / (34 * KC * 6);
-                const int gx = x0 - 1 + xh, gy = y0 - 1 + yh, gz = z0 - 1 + ez;
-                if ((unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz)
-                    val[j] = __ldg(reinterpret_cast<const uint4 *>(in + (((size_t)gx * ny + gy) * nz + gz) * CIN) + kc);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < kPer; ++j) {
-            const int e = tid + j * kTcThreads;
-            if (e < kChunks) {
-                const int ez = e % 34, kc = (e / 34) % KC, yh = (e / (34 * KC)) % 6, xh = e / (34 * KC * 6);
-                uint8_t *row = smem + ((kc * 3 + xh) * 6 + yh) * 512;
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const int zl = ez - d;
-                    if (zl >= 0 && zl < 32) *reinterpret_cast<uint4 *>(row + d * L::copy + zl * 16) = val[j];
+                    for (int kk = 0; kk < CIN / 16; ++kk)
+                        umma::mma_bf16(acc, umma::smem_desc(a0 + kk * 2 * kLboA, kLboA, 128),
+                                       umma::smem_desc(b0 + kk * 2 * kLboB, kLboB, 128), idesc, (t | kk) ? 1u : 0u);
                 }
+                umma::mma_commit(mbar + (i & 1));
             }
-        }
-        umma::fence_async_smem();
-        umma::fence_before_sync();
-        __syncthreads();
-        umma::fence_after_sync();
-        if (tid == 0) {
-            for (int t = 0; t < 27; ++t) {
-                const int dx = t / 9, dy = (t / 3) % 3, dz = t % 3;       // tap offset + 1
-                const uint32_t a0 = s_act + dz * L::copy + (dx * 6 + dy) * 512;
-                const uint32_t b0 = s_wts + t * L::tap;
-#pragma unroll
-                for (int kk = 0; kk < CIN / 16; ++kk)
-                    umma::mma_bf16(tmem, umma::smem_desc(a0 + kk * 2 * kLboA, kLboA, 128),
-                                   umma::smem_desc(b0 + kk * 2 * kLboB, kLboB, 128), idesc, (t | kk) ? 1u : 0u);
+            if (i > 0) {
+                const int p = (i - 1) & 1;
+                const bool ok = umma::mbar_wait(mbar + p, issued[p] & 1u, kTcWaitTries);
+                issued[p] += 1;
+                umma::fence_after_sync();
+                tile_epilogue<COUT, RELU, OUT_F32>(tmem, (uint32_t)(32 * p), ok, out, x - 1, y0, z0, ny, nz, warp,
+                                                   lane);
             }
-            umma::mma_commit(mbar);
-        }
-        const bool ok = umma::mbar_wait(mbar, parity, kTcWaitTries);
-        parity ^= 1u;
-        umma::fence_after_sync();
-        // warp w reads tensor-memory lanes 32 (w % 4) .. (rows: y0 + w % 4,
-        // z0 + lane), columns [16 (w / 4), 16 (w / 4) + 16) when COUT = 32
-        constexpr int CW = COUT / (kTcThreads / 128);               // columns per warp
-        const int quad = warp & 3, c_base = (warp >> 2) * CW;
-        static_assert(CW == 8 || CW == 16, "a warp reads 8 or 16 accumulator columns");
-        float v[CW];
-        if constexpr (CW == 16) umma::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c_base, v);
-        else umma::tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c_base, v);
-        if (!ok) {
-#pragma unroll
-            for (int i = 0; i < CW; ++i) v[i] = __int_as_float(0x7fc00000);
-        }
-        const int gy = y0 + quad, gz = z0 + lane;
-        if (gy < ny && gz < nz) {
-            const size_t vox = ((size_t)x0 * ny + gy) * nz + gz;
-            if constexpr (OUT_F32) {
-                float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + vox * COUT + c_base);
-#pragma unroll
-                for (int i = 0; i < CW / 4; ++i) {
-                    float4 q = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                    if (RELU) { q.x = fmaxf(q.x, 0.f); q.y = fmaxf(q.y, 0.f); q.z = fmaxf(q.z, 0.f); q.w = fmaxf(q.w, 0.f); }
-                    o[i] = q;
-                }
-            } else {
-                uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + vox * COUT + c_base);
-#pragma unroll
-                for (int i = 0; i < CW / 8; ++i) {
-                    uint32_t w[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        float a = v[8 * i + 2 * j], b = v[8 * i + 2 * j + 1];
-                        if (RELU) { a = fmaxf(a, 0.f); b = fmaxf(b, 0.f); }
-                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
-                        w[j] = *reinterpret_cast<const uint32_t *>(&h2);
-                    }
-                    o[i] = make_uint4(w[0], w[1], w[2], w[3]);
-                }
+            // plane x+2 (for tile x+1) into the buffer tile x-1 read; its MMAs are done
+            if (x + 2 <= xb) {
+                umma::fence_async_smem();
+                stage_plane<CIN>(smem + ((x + 2) & 3) * L::plane, in, x + 2, y0, z0, nx, ny, nz, tid);
             }
         }
         umma::fence_before_sync();
-        __syncthreads();                       // tensor memory and staged input free for the next tile
+        __syncthreads();                       // ring and accumulators free for the next run
         umma::fence_after_sync();
     }
-    if (warp == 0) umma::tmem_dealloc(tmem, 32);
+    if (warp == 0) umma::tmem_dealloc(tmem, 2 * 32);
 }
 
 // ------------------------------------------------------- weight gradient
@@ -397,23 +439,23 @@ static int sm_count()
 }
 
 // Launches the forward convolution (tcgen05 kernel) for a (CIN, COUT) pair:
-// persistent CTAs, as many per SM as the staged input and weights allow.
+// one persistent CTA per SM over runs of kSegX x planes.
 cudaError_t conv3d_forward(const __nv_bfloat16 *in, const __nv_bfloat16 *wk, void *out, int nx, int ny, int nz, int cin,
                            int cout, bool relu, bool out_f32, cudaStream_t st)
 {
-    const int tiles_y = (ny + 3) / 4, tiles_z = (nz + 31) / 32;
-    const int n_tiles = nx * tiles_y * tiles_z;
+    const int tiles_y = (ny + 3) / 4, tiles_z = (nz + 31) / 32, segs_x = (nx + kSegX - 1) / kSegX;
+    const int n_units = segs_x * tiles_y * tiles_z;
 #define TT_CONV_LAUNCH(CI, CO, R, F)                                                                  \
     do {                                                                                              \
         auto kern = k_conv3d_fwd_tc<CI, CO, R, F>;                                                    \
         constexpr uint32_t sm = TcConvSmem<CI, CO>::bytes;                                            \
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);             \
         const int per_sm = sm <= 110u * 1024u ? 2 : 1;                                                \
-        const int grid = n_tiles < sm_count() * per_sm ? n_tiles : sm_count() * per_sm;              \
-        kern<<<grid, kTcThreads, sm, st>>>(in, wk, out, nx, ny, nz, tiles_y, tiles_z, n_tiles);       \
+        const int grid = n_units < sm_count() * per_sm ? n_units : sm_count() * per_sm;              \
+        kern<<<grid, kTcThreads, sm, st>>>(in, wk, out, nx, ny, nz, tiles_y, tiles_z, segs_x, n_units); \
         return cudaGetLastError();                                                                    \
     } while (0)
-    if (n_tiles < 1) return cudaSuccess;
+    if (n_units < 1) return cudaSuccess;
     if (cin == 16 && cout == 32 && relu && !out_f32) TT_CONV_LAUNCH(16, 32, true, false);
     if (cin == 32 && cout == 32 && relu && !out_f32) TT_CONV_LAUNCH(32, 32, true, false);
     if (cin == 32 && cout == 16 && !relu && out_f32) TT_CONV_LAUNCH(32, 16, false, true);
