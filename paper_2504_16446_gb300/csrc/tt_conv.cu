@@ -49,59 +49,61 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
 
 // ------------------------------------------------ forward conv, tcgen05
 //
-// Implicit GEMM on the fifth-generation tensor cores: a tile is M = 128
-// output voxels (one x plane, four y rows of 32 z), N = COUT, K = 27 taps x
-// CIN.  For tap (dx, dy, dz) the A operand is the input shifted by the tap.
-// The tile's rows are 16 bytes apart (row m = 32 y + z), so a shift in y is
-// a change of the descriptor's start address (512 B per y row) and a shift
-// in x selects another staged plane; a shift in z would cross the ends of
-// the 32-voxel rows, so every plane is staged once per z shift: a plane
-// buffer is [dz 3][CIN/8][y 6][z 32] 16-byte (8-channel) chunks, zeros
-// outside the volume.  Core matrices: SBO = 128 B (next 8 rows), LBO = 6 *
-// 512 B (next 8 channels).  Weights are staged once per CTA as
-// [tap][CIN/8][COUT][8] (SBO = 128 B, LBO = COUT * 16 B).
+// Implicit GEMM on the fifth-generation tensor cores.  A tile covers one x
+// plane, four y rows and a window of 32 input z (z0-1 .. z0+30) whose inner
+// 30 are the tile's output z.  For each of the 9 in-plane tap offsets
+// (dx, dy) one MMA chain multiplies the 128 input rows (row m = 32 y + z,
+// 16 bytes apart, so a y offset is a change of descriptor start address and
+// an x offset another staged plane) by the three z taps' weights stacked as
+// N = 3 COUT columns:
+//   P_dz[row][co] = sum_{dx,dy,ci} x[x0+dx-1][y+dy-1][row z][ci] w[(dx,dy,dz)][co][ci]
+// and the epilogue applies the z taps by shifting rows between lanes:
+//   y(z) = P_0(z - 1) + P_1(z) + P_2(z + 1).
+// That is 9 * CIN / 16 MMAs of M 128, N 3 COUT, K 16 per tile, a third of
+// the count with the z taps as separate MMAs of N COUT; the MMA chain, not
+// the N width, sets the time at these sizes.  Plane buffers are [CIN/8][y 6]
+// [z 32] 16-byte (8-channel) chunks, zeros outside the volume: SBO = 128 B
+// (next 8 rows), LBO = 6 * 512 B (next 8 channels).  Weights are staged once
+// per CTA as [dx,dy][CIN/8][dz * COUT + co][8] (SBO = 128 B, LBO = 3 COUT
+// 16 B).
 //
-// Pipeline.  A persistent CTA walks runs of kSegX consecutive x planes of one
+// Pipeline.  A persistent CTA walks runs of seg_len consecutive x planes of one
 // (y, z) tile column.  Tile x needs planes x-1, x, x+1 from a ring of four
 // plane buffers, so each step stages one new plane.  Step for tile x: one
-// thread issues its 27 * CIN / 16 MMAs (M 128, N COUT, K 16) into
-// tensor-memory accumulator x % 2 and commits them to mbarrier x % 2; while
-// they run, all eight warps wait for tile x-1's mbarrier, write tile x-1 out
-// from its accumulator (ReLU, bf16 or f32), and stage plane x+2 into the
-// buffer that tile x-1 was the last to read.  A wait that gives up writes
-// NaN into its tile, which every consumer of the output sees.
+// thread issues its MMAs into tensor-memory accumulator x % 2 and commits
+// them to mbarrier x % 2; while they run, all eight warps wait for tile
+// x-1's mbarrier, write tile x-1 out (ReLU, bf16 or f32), and stage plane
+// x+2 into the buffer that tile x-1 was the last to read.  A wait that gives
+// up writes NaN into its tile, which every consumer of the output sees.
 constexpr uint32_t kTcWaitTries = 1u << 22;
 constexpr int kTcThreads = 256;
-constexpr int kSegX = 16;
+constexpr int kTileZ = 30;                 // output z per tile (32 input rows)
 
 template <int CIN, int COUT>
 struct TcConvSmem {
-    static constexpr uint32_t copy = (CIN / 8) * 6 * 512;     // one z-shifted copy of a plane
-    static constexpr uint32_t plane = 3 * copy;
-    static constexpr uint32_t tap = COUT * CIN * 2;            // one tap's weights
+    static constexpr uint32_t plane = (CIN / 8) * 6 * 512;
+    static constexpr uint32_t dxy = 3 * COUT * CIN * 2;       // weights of one (dx, dy): three z taps
     static constexpr uint32_t wts = 4 * plane;
-    static constexpr uint32_t mbar = wts + 27 * tap;
+    static constexpr uint32_t mbar = wts + 9 * dxy;
     static constexpr uint32_t bytes = mbar + 32;
+    static constexpr uint32_t tmem_cols = 2 * 3 * COUT <= 128 ? 128 : 256;   // two accumulators of 3 COUT
 };
 
-// Stages input plane gx (zeros outside the volume) into plane buffer `buf`:
-// each input chunk (y0-1+yh, z0-1+ez, channels 8 kc..) is loaded once, all of
-// a thread's loads in flight together, and stored into the copies d that use
-// it (z slot ez - d).
+// Stages input plane gx (zeros outside the volume) into a plane buffer:
+// chunk (kc, yh, zl) = voxel (gx, y0-1+yh, z0-1+zl), channels 8 kc .. 8 kc+7.
 template <int CIN>
 __device__ __forceinline__ void stage_plane(uint8_t *buf, const __nv_bfloat16 *__restrict__ in, int gx, int y0,
                                             int z0, int nx, int ny, int nz, int tid)
 {
-    constexpr int KC = CIN / 8, kChunks = 6 * 34 * KC, kPer = (kChunks + kTcThreads - 1) / kTcThreads;
-    constexpr uint32_t copy = KC * 6 * 512;
+    constexpr int KC = CIN / 8, kChunks = KC * 6 * 32, kPer = (kChunks + kTcThreads - 1) / kTcThreads;
     uint4 val[kPer];
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
         const int e = tid + j * kTcThreads;
         val[j] = make_uint4(0, 0, 0, 0);
         if (e < kChunks) {
-            const int ez = e % 34, kc = (e / 34) % KC, yh = e / (34 * KC);
-            const int gy = y0 - 1 + yh, gz = z0 - 1 + ez;
+            const int zl = e % 32, kc = (e / 32) % KC, yh = e / (32 * KC);
+            const int gy = y0 - 1 + yh, gz = z0 - 1 + zl;
             if ((unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz)
                 val[j] = __ldg(reinterpret_cast<const uint4 *>(in + (((size_t)gx * ny + gy) * nz + gz) * CIN) + kc);
         }
@@ -110,37 +112,40 @@ __device__ __forceinline__ void stage_plane(uint8_t *buf, const __nv_bfloat16 *_
     for (int j = 0; j < kPer; ++j) {
         const int e = tid + j * kTcThreads;
         if (e < kChunks) {
-            const int ez = e % 34, kc = (e / 34) % KC, yh = e / (34 * KC);
-            uint8_t *row = buf + (kc * 6 + yh) * 512;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const int zl = ez - d;
-                if (zl >= 0 && zl < 32) *reinterpret_cast<uint4 *>(row + d * copy + zl * 16) = val[j];
-            }
+            const int zl = e % 32, kc = (e / 32) % KC, yh = e / (32 * KC);
+            *reinterpret_cast<uint4 *>(buf + (kc * 6 + yh) * 512 + zl * 16) = val[j];
         }
     }
 }
 
-// Tile epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. (rows y0 +
-// w % 4, z0 + lane) and the w / 4-th half of the COUT columns of accumulator
-// `acc_col`.
+// Tile epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. (input rows
+// y0 + w % 4, z0 - 1 + lane) and, for its half of the output channels, the
+// three z-tap blocks of accumulator `acc_col`; lanes 1..30 combine rows
+// lane-1, lane, lane+1 and write output z0 - 1 + lane.
 template <int COUT, bool RELU, bool OUT_F32>
 __device__ __forceinline__ void tile_epilogue(uint32_t tmem, uint32_t acc_col, bool ok, void *__restrict__ out, int x0,
                                               int y0, int z0, int ny, int nz, int warp, int lane)
 {
     constexpr int CW = COUT / (kTcThreads / 128);
-    static_assert(CW == 8 || CW == 16, "a warp reads 8 or 16 accumulator columns");
+    static_assert(CW == 8 || CW == 16, "a warp reads 8 or 16 accumulator columns per z tap");
     const int quad = warp & 3, c_base = (warp >> 2) * CW;
-    float v[CW];
-    const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + acc_col + (uint32_t)c_base;
-    if constexpr (CW == 16) umma::tmem_ld16(taddr, v);
-    else umma::tmem_ld8(taddr, v);
-    if (!ok) {
+    const uint32_t lanes = (uint32_t)(quad * 32) << 16;
+    float p[3][CW];
 #pragma unroll
-        for (int i = 0; i < CW; ++i) v[i] = __int_as_float(0x7fc00000);
+    for (int dz = 0; dz < 3; ++dz) {
+        const uint32_t taddr = tmem + lanes + acc_col + (uint32_t)(dz * COUT + c_base);
+        if constexpr (CW == 16) umma::tmem_ld16(taddr, p[dz]);
+        else umma::tmem_ld8(taddr, p[dz]);
     }
-    const int gy = y0 + quad, gz = z0 + lane;
-    if (gy >= ny || gz >= nz) return;
+    float v[CW];
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+        const float below = __shfl_up_sync(0xffffffffu, p[0][c], 1);      // P_0 of row lane-1
+        const float above = __shfl_down_sync(0xffffffffu, p[2][c], 1);     // P_2 of row lane+1
+        v[c] = ok ? (below + p[1][c]) + above : __int_as_float(0x7fc00000);
+    }
+    const int gy = y0 + quad, gz = z0 - 1 + lane;
+    if (lane < 1 || lane > kTileZ || gy >= ny || gz >= nz) return;
     const size_t vox = ((size_t)x0 * ny + gy) * nz + gz;
     if constexpr (OUT_F32) {
         float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + vox * COUT + c_base);
@@ -170,35 +175,37 @@ __device__ __forceinline__ void tile_epilogue(uint32_t tmem, uint32_t acc_col, b
 template <int CIN, int COUT, bool RELU, bool OUT_F32>
 __global__ void __launch_bounds__(kTcThreads)
 k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ wk, void *__restrict__ out,
-                int nx, int ny, int nz, int tiles_y, int tiles_z, int segs_x, int n_units)
+                int nx, int ny, int nz, int tiles_y, int tiles_z, int seg_len, int segs_x, int n_units)
 {
     using L = TcConvSmem<CIN, COUT>;
-    constexpr int KC = CIN / 8;
-    constexpr uint32_t kLboA = 6 * 512, kLboB = COUT * 16;
+    constexpr int KC = CIN / 8, NB = 3 * COUT;
+    constexpr uint32_t kLboA = 6 * 512, kLboB = NB * 16;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L::mbar);   // [2]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    if (warp == 0) umma::tmem_alloc(tslot, 2 * 32);
+    if (warp == 0) umma::tmem_alloc(tslot, L::tmem_cols);
     if (tid == 0) { umma::mbar_init(mbar, 1); umma::mbar_init(mbar + 1, 1); }
-    for (int e = tid; e < 27 * COUT * KC; e += kTcThreads) {          // weights [t][co][ci] -> [t][ci/8][co][8]
+    // weights [t][co][ci], t = 9 dx + 3 dy + dz  ->  [dx,dy][ci/8][dz COUT + co][8]
+    for (int e = tid; e < 27 * COUT * KC; e += kTcThreads) {
         const int kc = e % KC, co = (e / KC) % COUT, t = e / (KC * COUT);
+        const int dxy = t / 3, dz = t % 3;
         const uint4 v = __ldg(reinterpret_cast<const uint4 *>(wk + ((size_t)t * COUT + co) * CIN) + kc);
-        *reinterpret_cast<uint4 *>(smem + L::wts + t * L::tap + kc * kLboB + co * 16) = v;
+        *reinterpret_cast<uint4 *>(smem + L::wts + dxy * L::dxy + kc * kLboB + (dz * COUT + co) * 16) = v;
     }
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
     const uint32_t tmem = *tslot;
-    const uint32_t idesc = umma::idesc_bf16_f32(128, COUT);
+    const uint32_t idesc = umma::idesc_bf16_f32(128, NB);
     const uint32_t s_planes = umma::smem_u32(smem), s_wts = umma::smem_u32(smem + L::wts);
-    uint32_t issued[2] = {0, 0};          // tiles committed per mbarrier (phase of the next wait)
+    uint32_t issued[2] = {0, 0};          // tiles waited per mbarrier (parity of the next wait)
 
     for (int unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
         const int sx = unit % segs_x, tz = (unit / segs_x) % tiles_z, ty = unit / (segs_x * tiles_z);
-        const int y0 = ty * 4, z0 = tz * 32, xa = sx * kSegX;
-        const int xb = min(nx, xa + kSegX);
+        const int y0 = ty * 4, z0 = tz * kTileZ, xa = sx * seg_len;
+        const int xb = min(nx, xa + seg_len);
         // planes xa-1, xa, xa+1 before the first tile (the ring is idle here)
         for (int px = xa - 1; px <= xa + 1; ++px)
             stage_plane<CIN>(smem + (px & 3) * L::plane, in, px, y0, z0, nx, ny, nz, tid);
@@ -209,15 +216,15 @@ k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__res
             __syncthreads();
             umma::fence_after_sync();
             if (x < xb && tid == 0) {
-                const uint32_t acc = tmem + (uint32_t)(32 * (i & 1));
-                for (int t = 0; t < 27; ++t) {
-                    const int dx = t / 9, dy = (t / 3) % 3, dz = t % 3;   // tap offset + 1
-                    const uint32_t a0 = s_planes + ((x - 1 + dx) & 3) * L::plane + dz * L::copy + dy * 512;
-                    const uint32_t b0 = s_wts + t * L::tap;
+                const uint32_t acc = tmem + (uint32_t)(NB * (i & 1));
+                for (int dxy = 0; dxy < 9; ++dxy) {
+                    const int dx = dxy / 3, dy = dxy % 3;                  // offset + 1
+                    const uint32_t a0 = s_planes + ((x - 1 + dx) & 3) * L::plane + dy * 512;
+                    const uint32_t b0 = s_wts + dxy * L::dxy;
 #pragma unroll
                     for (int kk = 0; kk < CIN / 16; ++kk)
                         umma::mma_bf16(acc, umma::smem_desc(a0 + kk * 2 * kLboA, kLboA, 128),
-                                       umma::smem_desc(b0 + kk * 2 * kLboB, kLboB, 128), idesc, (t | kk) ? 1u : 0u);
+                                       umma::smem_desc(b0 + kk * 2 * kLboB, kLboB, 128), idesc, (dxy | kk) ? 1u : 0u);
                 }
                 umma::mma_commit(mbar + (i & 1));
             }
@@ -226,7 +233,7 @@ k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__res
                 const bool ok = umma::mbar_wait(mbar + p, issued[p] & 1u, kTcWaitTries);
                 issued[p] += 1;
                 umma::fence_after_sync();
-                tile_epilogue<COUT, RELU, OUT_F32>(tmem, (uint32_t)(32 * p), ok, out, x - 1, y0, z0, ny, nz, warp,
+                tile_epilogue<COUT, RELU, OUT_F32>(tmem, (uint32_t)(NB * p), ok, out, x - 1, y0, z0, ny, nz, warp,
                                                    lane);
             }
             // plane x+2 (for tile x+1) into the buffer tile x-1 read; its MMAs are done
@@ -239,7 +246,7 @@ k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__res
         __syncthreads();                       // ring and accumulators free for the next run
         umma::fence_after_sync();
     }
-    if (warp == 0) umma::tmem_dealloc(tmem, 2 * 32);
+    if (warp == 0) umma::tmem_dealloc(tmem, L::tmem_cols);
 }
 
 // ------------------------------------------------------- weight gradient
@@ -439,23 +446,29 @@ static int sm_count()
 }
 
 // Launches the forward convolution (tcgen05 kernel) for a (CIN, COUT) pair:
-// one persistent CTA per SM over runs of kSegX x planes.
+// persistent CTAs (two per SM when the staging fits) over runs of seg_len x
+// planes; runs of 16 planes, shortened (to no fewer than 4) while there are
+// fewer than two runs per CTA.
 cudaError_t conv3d_forward(const __nv_bfloat16 *in, const __nv_bfloat16 *wk, void *out, int nx, int ny, int nz, int cin,
                            int cout, bool relu, bool out_f32, cudaStream_t st)
 {
-    const int tiles_y = (ny + 3) / 4, tiles_z = (nz + 31) / 32, segs_x = (nx + kSegX - 1) / kSegX;
-    const int n_units = segs_x * tiles_y * tiles_z;
+    const int tiles_y = (ny + 3) / 4, tiles_z = (nz + kTileZ - 1) / kTileZ;
 #define TT_CONV_LAUNCH(CI, CO, R, F)                                                                  \
     do {                                                                                              \
         auto kern = k_conv3d_fwd_tc<CI, CO, R, F>;                                                    \
-        constexpr uint32_t sm = TcConvSmem<CI, CO>::bytes;                                            \
+        /* at least 80 KB: no more than two CTAs share an SM's tensor memory */                     \
+        constexpr uint32_t sm = TcConvSmem<CI, CO>::bytes > 80u * 1024u ? TcConvSmem<CI, CO>::bytes   \
+                                                                        : 80u * 1024u;                 \
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);             \
-        const int per_sm = sm <= 110u * 1024u ? 2 : 1;                                                \
-        const int grid = n_units < sm_count() * per_sm ? n_units : sm_count() * per_sm;              \
-        kern<<<grid, kTcThreads, sm, st>>>(in, wk, out, nx, ny, nz, tiles_y, tiles_z, segs_x, n_units); \
+        const int slots = sm_count() * (sm <= 110u * 1024u ? 2 : 1);                                  \
+        int seg = 16;                                                                                 \
+        while (seg > 4 && ((nx + seg - 1) / seg) * tiles_y * tiles_z < 2 * slots) seg /= 2;           \
+        const int segs_x = (nx + seg - 1) / seg, n_units = segs_x * tiles_y * tiles_z;                \
+        const int grid = n_units < slots ? n_units : slots;                                           \
+        kern<<<grid, kTcThreads, sm, st>>>(in, wk, out, nx, ny, nz, tiles_y, tiles_z, seg, segs_x, n_units); \
         return cudaGetLastError();                                                                    \
     } while (0)
-    if (n_units < 1) return cudaSuccess;
+    if (nx < 1 || ny < 1 || nz < 1) return cudaSuccess;
     if (cin == 16 && cout == 32 && relu && !out_f32) TT_CONV_LAUNCH(16, 32, true, false);
     if (cin == 32 && cout == 32 && relu && !out_f32) TT_CONV_LAUNCH(32, 32, true, false);
     if (cin == 32 && cout == 16 && !relu && out_f32) TT_CONV_LAUNCH(32, 16, false, true);
