@@ -98,8 +98,43 @@ def iterations_to(h: tt.Handle, I, c0, L0: float, Lstar: float, target: float, m
     return it, ev, dt
 
 
+def conv_timing(n: int = 128, reps: int = 20):
+    """Device time of the network's forward convolutions on an n^3 volume
+    (tensor-core kernels through tt_conv3d_bf16, float output): per layer
+    shape, ms per launch and the dense-equivalent TFLOP/s."""
+    import ctypes
+    lib = tt.load()
+    out = {}
+    for cin, cout in ((16, 32), (32, 32), (32, 16)):
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(cin * 100 + cout)
+        x = torch.randn((n, n, n, cin), device="cuda", generator=gen).to(torch.bfloat16)
+        w = (0.1 * torch.randn((27, cout, cin), device="cuda", generator=gen)).to(torch.bfloat16)
+        y = torch.empty((n, n, n, cout), device="cuda", dtype=torch.float32)
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+        def run():
+            st = lib.tt_conv3d_bf16(n, n, n, cin, cout, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+                                    0, ctypes.c_void_p(y.data_ptr()), stream)
+            if st != tt.TT_OK:
+                raise tt.TTError(st, "tt_conv3d_bf16", lib.tt_last_error().decode())
+        for _ in range(3):
+            run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            run()
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[f"{cin}->{cout}"] = {"ms": ms, "tflops": 2.0 * n ** 3 * 27 * cin * cout / (ms * 1e9)}
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
+    ap.add_argument("--conv-timing", type=int, default=0, metavar="N",
+                    help="only time the forward convolutions on an N^3 volume and exit")
     ap.add_argument("--train", type=int, default=512)
     ap.add_argument("--test", type=int, default=32)
     ap.add_argument("--epochs", type=int, default=6)
@@ -107,6 +142,10 @@ def main(argv=None):
     ap.add_argument("--ref-iters", type=int, default=150, help="L-BFGS iterations defining L* of a test phantom")
     ap.add_argument("--lr", type=float, default=1e-3)
     args = ap.parse_args(argv)
+    if args.conv_timing:
+        print(json.dumps({"experiment": "forward convolution timing", "volume": f"{args.conv_timing}^3",
+                          "layers": conv_timing(args.conv_timing)}))
+        return
 
     # training: 64^3, l_max 4, 120 projections of 64x64 x 16 segments, seeds 100..
     st_tr = synth.workload("ell64")
