@@ -80,14 +80,18 @@ def peaks():
 
 
 def _kernel_source_hash():
-    """Hash of the sources of the forward and adjoint kernels (their templates,
-    constants and the FP32 instantiation) that the ncu traffic belongs to."""
+    """Hash of the code (comments and blank space removed) of the forward and
+    adjoint kernels -- their templates, constants and the FP32 instantiation
+    -- that the ncu traffic belongs to."""
     import hashlib
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2504_16446_gb300", "csrc")
     for f in ("tt_internal.cuh", "tt_kernels.cuh", "tt_proj_f32.cu"):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, f)) as fh:
+            code = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        code = re.sub(r"//[^\n]*", "", code)
+        h.update("".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -38,10 +38,11 @@ __host__ __device__ constexpr int adjoint_voxels(int KP, int LG)
 //   plane p (index along the main axis m), ray (j,k):
 //     u(j,k,p) = u0 + j*uj + k*uk + p*up   (continuous index along axis u)
 //     v(j,k,p) = v0 + j*vj + k*vk + p*vp   (continuous index along axis v)
-//   adjoint: the ray lattice point nearest to voxel (U,V) on plane p is
+//   adjoint: the detector point whose ray crosses plane p at voxel (U,V) is
 //     jc = jc0 + jU*U + jV*V + jP*p,  kc = kc0 + kU*U + kV*V + kP*p,
 //   and every ray that has (U,V) as a bilinear tap lies in
-//     |j - jc| < hj, |k - kc| < hk   (at most nwj x nwk candidates).
+//     |j - jc| < hj, |k - kc| < hk   (the bounding box of the parallelogram
+//   |du| < 1, |dv| < 1 in detector coordinates).
 struct ProjGeom {
     double u0, uj, uk, up;
     double v0, vj, vk, vp;
