@@ -139,6 +139,25 @@ def test_loss_is_the_same_with_and_without_gradient(prec):
     assert torch.isfinite(g).all()
 
 
+@pytest.mark.parametrize("prec,n_proj", [("f32", 300), ("f64", 200)])
+def test_adjoint_over_several_parameter_blocks(prec, n_proj):
+    """More projections than one adjoint launch holds in its parameter block
+    (256 for FP32, 128 for FP64): the launches accumulate in the handle's
+    padded gradient and the last one writes the result."""
+    st = synth.small_setup(n=(7, 6, 9), nj=8, nk=7, ell_max=4, n_proj=n_proj, n_seg=5, seed=41)
+    dt, tol = (torch.float32, F32_TOL) if prec == "f32" else (torch.float64, F64_TOL)
+    c = synth.random_volume(st, 42)
+    I = synth.random_data(st, 43)
+    W = synth.random_weights(st, 44)
+    loss_ref, g_ref = oracle.gradient_residual(oracle_geometry(st), c, I, W)
+    h = tt.Handle(st, prec)
+    loss, g = h.gradient_residual(dev(c, dt), dev(I, dt), dev(W, dt))
+    assert abs(loss - loss_ref) <= tol * abs(loss_ref)
+    assert rel_l2(g.cpu().numpy(), g_ref) <= tol
+    R = synth.random_data(st, 45)
+    assert rel_l2(h.adjoint(dev(R, dt)).cpu().numpy(), oracle.adjoint(oracle_geometry(st), R)) <= tol
+
+
 def test_adjoint_identity_on_gpu_fp64():
     st = synth.small_setup(n=(14, 12, 13), nj=15, nk=17, ell_max=4, n_proj=11, n_seg=6, seed=8)
     h = tt.Handle(st, "f64")
