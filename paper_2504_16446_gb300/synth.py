@@ -97,6 +97,9 @@ def geometry_angles(name: str):
     elif name == "ply100":      # 45 rotations 8 deg apart x tilts {0,15,30,45}
         al = [8.0 * i for t in range(4) for i in range(45)]
         be = [15.0 * t for t in range(4) for _ in range(45)]
+    elif name == "paper247":    # 19 rotations (360/19 deg apart, offset 1.5 deg per tilt) x 13 tilts 0..45 deg
+        al = [360.0 / 19 * i + 1.5 * t for t in range(13) for i in range(19)]
+        be = [3.75 * t for t in range(13) for _ in range(19)]
     else:
         raise KeyError(name)
     return al, be
@@ -110,7 +113,20 @@ def workload(name: str) -> Setup:
     ell128  128^3, l_max 8, 240 projections of 128x128, 8 segments
     ply100  100^3, l_max 6, 180 projections of 100x100, 8 segments
     ell128c16  128^3, l_max 4, ell128 geometry with 16 segments
+    paper247_l{2,4,8}  the paper's dataset shape: 247 projections of 65 (j,
+               along the rotation axis y) x 55 (k) pixels x 8 segments; the
+               volume, 55 x 65 x 55, and the 19 x 13 tilt series are guesses
+               (the paper states neither)
     """
+    if name.startswith("paper247_l"):
+        ell = int(name[len("paper247_l"):])
+        s0, s1 = segments(8)
+        al, be = geometry_angles("paper247")
+        S = len(al)
+        return Setup(shape=(55, 65, 55), nj=65, nk=55, ell_max=ell,
+                     inner_angle=np.deg2rad(np.asarray(al, dtype=np.float64)),
+                     outer_angle=np.deg2rad(np.asarray(be, dtype=np.float64)),
+                     seg_start=s0, seg_end=s1, j_offset=np.zeros(S), k_offset=np.zeros(S))
     if name == "cyl16":
         return _setup(16, 16, 2, *geometry_angles("cyl16"), 8)
     if name == "ell64":
