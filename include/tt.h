@@ -58,12 +58,12 @@ typedef enum {
 
 /* Precision of a handle.  TT_F32 and TT_F64: storage and arithmetic in that
  * type.  TT_BF16 and TT_F16 (the reduced-precision form): the entry points
- * take and return float like TT_F32, but the coefficient volume and the
- * back-contracted residual are stored inside the path as bfloat16 / float16
- * (halving their traffic), with float arithmetic, Kahan-compensated ray
- * sums, and FP64 loss and dot-product reductions.  Their results differ from
- * FP32 by the 2-byte rounding of those two intermediates (relative ~1e-3 for
- * bfloat16, ~1e-4 for float16). */
+ * take and return float like TT_F32, but the coefficient volume that the
+ * forward projector marches through is stored inside the path as bfloat16 /
+ * float16 (halving the projector's volume traffic and footprint), with float
+ * arithmetic and FP64 loss and dot-product reductions; the back-contracted
+ * residual stays float.  Their results differ from FP32 by the 2-byte
+ * rounding of the volume (relative ~1e-3 for bfloat16, ~1e-4 for float16). */
 typedef enum { TT_F32 = 0, TT_F64 = 1, TT_BF16 = 2, TT_F16 = 3 } tt_precision;
 
 /* Unit vectors of the instrument in laboratory coordinates, Table

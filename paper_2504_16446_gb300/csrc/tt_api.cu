@@ -490,7 +490,7 @@ tt_status tt_create(const tt_problem *P, tt_precision prec, void *stream, tt_han
         if (ez != cudaSuccess) { free_handle(h); return cuda_fail(ez, "tt_create: memset"); }
     }
     ALLOC(h->gpad, es * h->nvox() * h->KP);
-    ALLOC(h->G, h->ssize() * h->npix() * h->KP);
+    ALLOC(h->G, es * h->npix() * h->KP);
     h->n_fwd_ctas = forward_ctas(h);
     h->n_partials = h->n_fwd_ctas;
     ALLOC(h->partials, sizeof(double) * h->n_partials);

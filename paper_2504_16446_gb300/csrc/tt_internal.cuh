@@ -129,7 +129,7 @@ struct tt_handle {
     long long npix() const { return (long long)S * nj * nk; }
     long long ndata() const { return npix() * C; }
     size_t esize() const { return prec == TT_F64 ? 8 : 4; }                 // API element
-    size_t ssize() const { return prec == TT_BF16 || prec == TT_F16 ? 2 : esize(); }  // cpad, G storage
+    size_t ssize() const { return prec == TT_BF16 || prec == TT_F16 ? 2 : esize(); }  // cpad storage
 };
 
 namespace tt {
@@ -181,8 +181,9 @@ template <typename T, typename S>
 cudaError_t launch_pack(tt_handle *h, const T *c);
 template <typename T>
 cudaError_t launch_unpack(tt_handle *h, const T *gpad, T *g);
-// Projector launchers: arithmetic in T, the coefficient volume cpad and the
-// back-contracted residual G stored as S (S = T, or a 2-byte type for T = float).
+// Projector launchers: arithmetic in T, the coefficient volume cpad stored as
+// S (S = T, or a 2-byte type for T = float); the back-contracted residual G
+// is T.
 // Projections [s0, s1) only (s1 < 0: to the last); the gradient mode writes
 // the loss partials of those projections' CTAs.
 template <typename T, typename S>

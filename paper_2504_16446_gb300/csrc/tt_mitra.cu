@@ -153,7 +153,7 @@ tt_status sirt_weights_impl(tt_handle *h, const T *W, T *R, T *D)
         prof_begin(h, TT_KSLOT_VECTOR, &ev);
         k_row_weights<T><<<blocks_for(h->ndata()), 256, 0, h->stream>>>(R, W, (const T *)h->Bp, row_abs, h->ndata(),
                                                                       npix_s, h->C, h->CP, h->KP, 1e-6 * h->a);
-        k_fill_G<S><<<blocks_for(h->npix() * h->KP), 256, 0, h->stream>>>((S *)h->G, col_abs, h->npix() * h->KP,
+        k_fill_G<T><<<blocks_for(h->npix() * h->KP), 256, 0, h->stream>>>((T *)h->G, col_abs, h->npix() * h->KP,
                                                                         npix_s, h->KP);
         e = cudaGetLastError();
         prof_end(h, TT_KSLOT_VECTOR, ev);
