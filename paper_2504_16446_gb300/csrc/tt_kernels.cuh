@@ -717,7 +717,9 @@ cudaError_t launch_backcontract_L(tt_handle *h, const T *R)
 template <typename T, typename S, int L>
 cudaError_t launch_adjoint_L(tt_handle *h, T *g, bool reduce_loss)
 {
-    constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K), V = adjoint_voxels(KP, LG);
+    // For K <= 8 a single lane owns a voxel and reads its whole (32-byte) G
+    // row: no candidate exchange, measured 7% faster than two-lane groups.
+    constexpr int K = num_coeffs(L), KP = padded_k(K), LG = K <= 8 ? 1 : lane_group(K), V = adjoint_voxels(KP, LG);
     constexpr int BZ = (32 / LG) * V, BY = 4, BX = (kThreads / 32) / BY;
     const int tx = (h->N[0] + BX - 1) / BX, ty = (h->N[1] + BY - 1) / BY, tz = (h->N[2] + BZ - 1) / BZ;
     const std::vector<AdjParams<T>> &chunks = adj_params<T>(h);
