@@ -80,7 +80,7 @@ typedef struct {
 typedef struct {
     int nx, ny, nz;              /* volume shape (voxels), each >= 1            */
     int nj, nk;                  /* raster pixels per projection, each >= 1    */
-    int n_proj;                  /* projections s, >= 1                         */
+    int n_proj;                  /* projections s, 1..65535                     */
     int ell_max;                 /* even band limit, 0..12                      */
     int n_seg;                   /* detector segments c, 1..64                  */
     const double *inner_angle;   /* alpha_s [n_proj], radians                   */
@@ -91,7 +91,7 @@ typedef struct {
     const double *seg_end;       /* phi_c,end   [n_seg], radians, > start       */
     double two_theta;            /* scattering angle 2 theta, radians           */
     double voxel_size;           /* a > 0                                       */
-    double step_size;            /* b > 0                                       */
+    double step_size;            /* b >= a / 50                                 */
     tt_frame frame;
 } tt_problem;
 
@@ -105,7 +105,13 @@ const char *tt_status_string(tt_status s);
 /* Message of the last failing call on this host thread ("" if none). */
 const char *tt_last_error(void);
 
-/* Validates the problem, copies it, computes the per-projection ray
+/* Limits checked here (TT_INVALID_ARG otherwise): nx*ny*nz <= 2^24 voxels,
+ * 1 <= n_proj <= 65535, ell_max even and >= 0 (above 12: TT_UNSUPPORTED),
+ * 1 <= n_seg <= 64, finite
+ * angles and offsets, seg_end > seg_start, a > 0, b >= a / 50 (finer
+ * detector pixels would put hundreds of rays on each voxel), orthonormal
+ * p, j, k and q0, q90 _|_ p.
+ * Validates the problem, copies it, computes the per-projection ray
  * constants (host, FP64) and the basis matrix (device, FP64, see
  * tt_basis_matrix), and allocates the handle's device scratch.  stream is a
  * cudaStream_t (NULL = legacy default stream); the current CUDA device at
