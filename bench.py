@@ -336,7 +336,7 @@ def make_inputs(st, torch, tt, synth):
     I = (torch.poisson(clean.clamp(min=0) * scale, generator=gen) / scale).contiguous()
     W = torch.ones_like(I)
     c = (0.5 * c_true).contiguous()
-    return h, c, I, W
+    return h, c, I, W, c_true
 
 
 def reference_loss(h, I, W, torch, tt, ref_iters: int):
@@ -408,6 +408,31 @@ def mitra_vs_lbfgs(h, I, W, torch, tt, ref_iters: int, target: float = 1e-3, max
             "lbfgs": {k: lb[k] for k in ("seconds", "iterations", "evals", "reached")}}
 
 
+def noise_free_residual(h, c_true, torch, tt, target: float = 1e-3, max_iter: int = 500):
+    """The literal criterion on noise-free data I = A c_true: L-BFGS from
+    zero until the relative data residual |A c - I| / |I| <= target
+    (computed from the loss, W = 1).  Wall time, iterations, evaluations."""
+    I = h.project(c_true)
+    nI = float(torch.linalg.vector_norm(I.double()))
+    z = torch.zeros(h.volume_shape, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    opt = tt.LBFGS(h, z, I, None, m=10)
+    it, ev = 0, 1
+    while opt.loss ** 0.5 > target * nI and it < max_iter:
+        _, ne, st_ = opt.step()
+        it += 1
+        ev += ne
+        if st_ != tt.TT_OK:
+            break
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    rel = opt.loss ** 0.5 / nI
+    opt.close()
+    return {"criterion": f"|A c - I| / |I| <= {target:g} on noise-free data", "seconds": dt, "iterations": it,
+            "evals": ev, "relative_residual": rel, "reached": bool(rel <= target)}
+
+
 def measure_forms(torch, tt, synth, flush, steps: int = 20):
     """ms per gradient evaluation of the FP32, bfloat16- and float16-storage
     forms on the 64^3 (l_max 4) and 128^3 (l_max 8, 240 x 128^2 x 8) workloads;
@@ -462,7 +487,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     st = synth.workload(WORKLOAD)
-    h, c, I, W = make_inputs(st, torch, tt, synth)
+    h, c, I, W, c_true = make_inputs(st, torch, tt, synth)
     g = torch.empty_like(c)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     for _ in range(max(args.warmup, 3)):
@@ -575,6 +600,7 @@ def run_ours(args):
         out["time_to_loss"]["bf16"] = time_to_loss(hb, I, W, torch, tt, args.ttl_ref_iters, L0_Lstar=ref)
         hb.close()
         out["time_to_loss"]["sirt_weighted"] = mitra_vs_lbfgs(h, I, W, torch, tt, args.ttl_ref_iters)
+        out["time_to_loss"]["noise_free"] = noise_free_residual(h, c_true, torch, tt)
     out["standalone"] = standalone(h, c, I, torch, flush)
     if not args.no_forms:
         out["forms"] = measure_forms(torch, tt, synth, flush)
