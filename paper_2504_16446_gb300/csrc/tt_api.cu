@@ -36,19 +36,70 @@ static tt_status invalid(const std::string &msg)
     return TT_INVALID_ARG;
 }
 
+// Launch timing with CUDA events.  Events come from a free list that is
+// filled when profiling is switched on, and before each new launch up to two
+// recorded pairs whose end event has completed are folded into the totals,
+// so that a long timed loop neither creates events nor grows the list of
+// pairs: its cost is two event records and a query or two per launch.
+static constexpr size_t kProfileEvents = 256;
+
+// Folds up to max_pairs pairs, oldest first, into the totals.  With wait,
+// waits for them; otherwise stops at the first pair still in flight.
+static cudaError_t prof_fold(tt_handle *h, bool wait, size_t max_pairs)
+{
+    auto &P = h->prof;
+    for (size_t n = 0; n < max_pairs && !P.pending.empty(); ++n) {
+        const tt::Profile::Pending r = P.pending.front();
+        if (!wait) {
+            const cudaError_t q = cudaEventQuery(r.end);
+            if (q == cudaErrorNotReady) {
+                (void)cudaGetLastError();   // "not ready" is no error: keep it out of the launch checks
+                break;
+            }
+            if (q != cudaSuccess) return q;
+        }
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.end);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.begin, r.end);
+        if (e != cudaSuccess) return e;
+        P.total_ms[r.slot] += ms;
+        P.launches[r.slot] += 1;
+        P.free_events.push_back(r.begin);
+        if (r.free_end) P.free_events.push_back(r.end);
+        P.pending.pop_front();
+    }
+    return cudaSuccess;
+}
+
+static cudaEvent_t prof_event(tt_handle *h)
+{
+    auto &P = h->prof;
+    prof_fold(h, false, 2);
+    if (P.free_events.empty()) {
+        cudaEvent_t e;
+        return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+    }
+    cudaEvent_t e = P.free_events.back();
+    P.free_events.pop_back();
+    return e;
+}
+
 void prof_begin(tt_handle *h, int slot, cudaEvent_t *ev)
 {
     (void)slot;
     ++h->launch_count;
     *ev = nullptr;
-    if (!h->prof.enabled) return;
-    cudaEvent_t e;
-    if (!h->prof.free_events.empty()) {
-        e = h->prof.free_events.back();
-        h->prof.free_events.pop_back();
-    } else if (cudaEventCreate(&e) != cudaSuccess) {
+    auto &P = h->prof;
+    if (!P.enabled) return;
+    if (P.chain && P.last_end) {
+        // the previous launch's end event, the back pair of the list
+        *ev = P.last_end;
+        P.pending.back().free_end = false;
+        P.last_end = nullptr;
         return;
     }
+    cudaEvent_t e = prof_event(h);
+    if (!e) return;
     cudaEventRecord(e, h->stream);
     *ev = e;
 }
@@ -56,18 +107,26 @@ void prof_begin(tt_handle *h, int slot, cudaEvent_t *ev)
 void prof_end(tt_handle *h, int slot, cudaEvent_t ev)
 {
     if (!h->prof.enabled || ev == nullptr) return;
-    cudaEvent_t e;
-    if (!h->prof.free_events.empty()) {
-        e = h->prof.free_events.back();
-        h->prof.free_events.pop_back();
-    } else if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaEvent_t e = prof_event(h);
+    if (!e) {
         h->prof.free_events.push_back(ev);
         return;
     }
     cudaEventRecord(e, h->stream);
-    h->prof.pool.push_back(ev);
-    h->prof.pool.push_back(e);
-    h->prof.pool_slot.push_back(slot);
+    h->prof.pending.push_back({ev, e, slot, true});
+    h->prof.last_end = h->prof.chain ? e : nullptr;
+}
+
+ProfChain::ProfChain(tt_handle *h_) : h(h_)
+{
+    h->prof.chain = true;
+    h->prof.last_end = nullptr;
+}
+
+ProfChain::~ProfChain()
+{
+    h->prof.chain = false;
+    h->prof.last_end = nullptr;
 }
 
 // ---------------------------------------------------------------- geometry
@@ -310,7 +369,10 @@ static void free_handle(tt_handle *h)
     for (cudaStream_t t : h->side)
         if (t) cudaStreamDestroy(t);
     if (h->loss_pinned) cudaFreeHost(h->loss_pinned);
-    for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+    for (const auto &r : h->prof.pending) {
+        cudaEventDestroy(r.begin);
+        if (r.free_end) cudaEventDestroy(r.end);
+    }
     for (cudaEvent_t e : h->prof.free_events) cudaEventDestroy(e);
     delete h;
 }
@@ -343,6 +405,7 @@ static tt_status project_impl(tt_handle *h, const T *c, T *I)
 {
     if (bad_ptr(c) || bad_ptr(I)) return invalid("tt_project: device pointers must be non-null and 16-byte aligned");
     return with_storage<T>(h, [&]<typename S>() -> tt_status {
+        const ProfChain chain(h);   // pack, forward and adjoint run back to back
         TT_CUDA((launch_pack<T, S>(h, c)), "pack");
         TT_CUDA((launch_forward<T, S>(h, I, nullptr, nullptr, false)), "forward");
         return TT_OK;
@@ -371,6 +434,7 @@ tt_status tt_grad_enqueue(tt_handle *h, const T *c, const T *I, const T *W, T *g
     if (bad_ptr(c) || bad_ptr(I) || (W && bad_ptr(W)) || (g && bad_ptr(g)))
         return invalid("tt_gradient_residual: device pointers must be non-null (W, g may be NULL) and 16-byte aligned");
     return with_storage<T>(h, [&]<typename S>() -> tt_status {
+        const ProfChain chain(h);   // pack, forward and adjoint run back to back
         TT_CUDA((launch_pack<T, S>(h, c)), "pack");
         TT_CUDA((launch_forward<T, S>(h, nullptr, I, W, true)), "forward");
         // the adjoint's first CTA reduces the loss partials; without a
@@ -689,6 +753,11 @@ tt_status tt_profile_enable(tt_handle *h, int enable)
 {
     if (!h) return invalid("null handle");
     h->prof.enabled = enable != 0;
+    while (h->prof.enabled && h->prof.free_events.size() + 2 * h->prof.pending.size() < kProfileEvents) {
+        cudaEvent_t e;
+        TT_CUDA(cudaEventCreate(&e), "event create");
+        h->prof.free_events.push_back(e);
+    }
     return TT_OK;
 }
 
@@ -696,9 +765,11 @@ tt_status tt_profile_reset(tt_handle *h)
 {
     if (!h) return invalid("null handle");
     TT_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
-    for (cudaEvent_t e : h->prof.pool) h->prof.free_events.push_back(e);
-    h->prof.pool.clear();
-    h->prof.pool_slot.clear();
+    for (const auto &r : h->prof.pending) {
+        h->prof.free_events.push_back(r.begin);
+        if (r.free_end) h->prof.free_events.push_back(r.end);
+    }
+    h->prof.pending.clear();
     for (int i = 0; i < TT_KSLOT_COUNT; ++i) { h->prof.total_ms[i] = 0.0; h->prof.launches[i] = 0; }
     return TT_OK;
 }
@@ -707,18 +778,7 @@ tt_status tt_profile_read(tt_handle *h, int slot, double *total_ms, long long *l
 {
     if (!h) return invalid("null handle");
     if (slot < 0 || slot >= TT_KSLOT_COUNT) return invalid("bad kernel slot");
-    if (!h->prof.pool.empty()) {
-        TT_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
-        for (size_t i = 0; i < h->prof.pool_slot.size(); ++i) {
-            float ms = 0.f;
-            TT_CUDA(cudaEventElapsedTime(&ms, h->prof.pool[2 * i], h->prof.pool[2 * i + 1]), "event elapsed");
-            h->prof.total_ms[h->prof.pool_slot[i]] += ms;
-            h->prof.launches[h->prof.pool_slot[i]] += 1;
-        }
-        for (cudaEvent_t e : h->prof.pool) h->prof.free_events.push_back(e);
-        h->prof.pool.clear();
-        h->prof.pool_slot.clear();
-    }
+    TT_CUDA(prof_fold(h, true, (size_t)-1), "profile events");
     if (total_ms) *total_ms = h->prof.total_ms[slot];
     if (launches) *launches = h->prof.launches[slot];
     return TT_OK;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <deque>
 #include <string>
 #include <vector>
 
@@ -82,9 +83,17 @@ struct AdjParams {
 };
 
 struct Profile {
+    struct Pending {
+        cudaEvent_t begin, end;
+        int slot;
+        bool free_end;                 // false when `end` is also the next pair's begin
+    };
     bool enabled = false;
-    std::vector<cudaEvent_t> pool;     // recorded pairs awaiting read
-    std::vector<int> pool_slot;
+    // Inside a chain of back-to-back launches on the stream (nothing else
+    // enqueued between them), a launch's end event is the next one's begin.
+    bool chain = false;
+    cudaEvent_t last_end = nullptr;
+    std::deque<Pending> pending;       // recorded pairs, oldest first, not yet folded into the totals
     std::vector<cudaEvent_t> free_events;
     double total_ms[TT_KSLOT_COUNT] = {};
     long long launches[TT_KSLOT_COUNT] = {};
@@ -174,6 +183,15 @@ const std::vector<AdjParams<double>> &adj_params<double>(const tt_handle *h);
 // Bracket a kernel launch with the handle's profiling events.
 void prof_begin(tt_handle *h, int slot, cudaEvent_t *ev);
 void prof_end(tt_handle *h, int slot, cudaEvent_t ev);
+// While alive, the handle's launches share boundary events (the launches it
+// covers must be enqueued back to back on the handle's stream).
+struct ProfChain {
+    tt_handle *h;
+    explicit ProfChain(tt_handle *h_);
+    ~ProfChain();
+    ProfChain(const ProfChain &) = delete;
+    ProfChain &operator=(const ProfChain &) = delete;
+};
 
 // Kernel launchers (return the launch error, if any).
 // Packs c [nvox][K] into the interior of cpad (channels padded to KP).
