@@ -167,6 +167,54 @@ __device__ __forceinline__ void dot2_add(Dot2 &a, float x, float y)
 
 __device__ __forceinline__ double dot2_value(const Dot2 &a) { return (double)a.s + (double)a.c; }
 
+// a += x, compensated (Dot2's summation step alone).
+__device__ __forceinline__ void dot2_add1(Dot2 &a, float x)
+{
+    const float t = __fadd_rn(a.s, x);
+    const float z = __fsub_rn(t, a.s);
+    const float e = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, z)), __fsub_rn(x, z));
+    a.s = t;
+    a.c = __fadd_rn(a.c, e);
+}
+
+// (s, c) + (s', c') with the same compensation: TwoSum of the leading parts,
+// the error added to the sum of the trailing parts.
+__device__ __forceinline__ Dot2 dot2_merge(Dot2 a, Dot2 b)
+{
+    Dot2 r = a;
+    dot2_add1(r, b.s);
+    r.c = __fadd_rn(r.c, b.c);
+    return r;
+}
+
+// Deterministic (fixed-order) block sum of one compensated pair per thread,
+// in FP32 arithmetic: a warp tree of dot2_merge, the warps' results merged
+// by warp 0.  The one conversion to FP64 happens at the end; on this GPU an
+// FP64 shuffle tree per CTA costs tens of times more issue time in the FP64
+// pipe than the same tree in FP32.  red: one Dot2 of shared memory per warp;
+// the leading barrier lets a CTA call it several times in a row.  Result
+// valid on thread 0.
+__device__ __forceinline__ double dot2_block_sum(Dot2 v, Dot2 *red)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const Dot2 o = {__shfl_down_sync(0xffffffffu, v.s, off), __shfl_down_sync(0xffffffffu, v.c, off)};
+        v = dot2_merge(v, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    if (w != 0) return 0.0;
+    Dot2 t = l < (int)(blockDim.x >> 5) ? red[l] : Dot2{0.f, 0.f};
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const Dot2 o = {__shfl_down_sync(0xffffffffu, t.s, off), __shfl_down_sync(0xffffffffu, t.c, off)};
+        t = dot2_merge(t, o);
+    }
+    return l == 0 ? dot2_value(t) : 0.0;
+}
+
 void set_error(const std::string &msg);
 tt_status cuda_fail(cudaError_t e, const char *what);
 // Problem validation and Gauss-Legendre rule shared by the entry points.

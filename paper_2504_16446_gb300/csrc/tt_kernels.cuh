@@ -366,8 +366,11 @@ k_forward(const ProjGeom *__restrict__ geo, const S *__restrict__ cpad /* interi
     const long long pix = ((long long)s * nj + j) * nk + k;
     const T lossr = forward_epilogue<T, S, CPL, KP, LG, GRAD>(acc, q, valid, true, pix, Bs, C, CP, Iout, Id, Wd, G);
     if constexpr (GRAD) {
-        const double lv = (q == 0 && valid) ? (double)lossr : 0.0;
-        const double tot = block_sum(lv, red);
+        double tot;
+        if constexpr (std::is_same<T, float>::value)
+            tot = dot2_block_sum(Dot2{(q == 0 && valid) ? lossr : 0.f, 0.f}, reinterpret_cast<Dot2 *>(red));
+        else
+            tot = block_sum((q == 0 && valid) ? (double)lossr : 0.0, red);
         // canonical CTA index (projection, j tile, k tile): the same for
         // either CTA order and for chunked launches, so the loss sums alike
         if (threadIdx.x == 0) partials[((long long)s * tiles_j + tj) * tiles_k + tk] = tot;

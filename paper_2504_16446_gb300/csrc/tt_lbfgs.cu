@@ -37,13 +37,40 @@ using namespace tt;
 namespace {
 
 constexpr int kMaxM = 64;
-constexpr int kPairBlocks = 304;   // CTAs of the pair / cross dot kernels (2 x 152 SMs)
+#ifndef TT_PAIR_BLOCKS
+#define TT_PAIR_BLOCKS 608
+#endif
+constexpr int kPairBlocks = TT_PAIR_BLOCKS;   // CTAs of the pair / cross dot kernels (4 per SM)
 
-// Blocks of the per-element kernels: a multiple of the SM count, capped.
+// Blocks of the per-element kernels (four elements per thread): a multiple of
+// the SM count, capped.
 unsigned elem_blocks(long long n)
 {
-    long long b = (n + 255) / 256;
+    long long b = (n / 4 + 255) / 256;
     return (unsigned)std::max(1LL, std::min(b, 152LL * 16));
+}
+
+// Four consecutive elements as one 16-byte access (two for double).  Every
+// vector of the solver starts on a 256-byte boundary, so element 4q is
+// 16-byte aligned.
+__device__ __forceinline__ void ld4(const float *__restrict__ p, float (&v)[4])
+{
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void ld4(const double *__restrict__ p, double (&v)[4])
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float *__restrict__ p, const float (&v)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double *__restrict__ p, const double (&v)[4])
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
 }
 
 // Block sum of a double, result on thread 0 (blockDim 256).
@@ -70,17 +97,39 @@ struct Combo {
     int n;
 };
 
-// d = sum_i c_i v_i (in T, coefficients rounded to T), xt = x + a d.
+// d = sum_i c_i v_i (in T, coefficients rounded to T, summed in order i),
+// xt = x + a d; four elements per thread and step, the last n % 4 elements
+// by the first threads.
 template <typename T>
 __global__ void k_direction(const __grid_constant__ Combo<T> cb, const T *__restrict__ x, T *__restrict__ d,
                             T *__restrict__ xt, double a, long long n)
 {
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x) {
-        T s = T(0);
-        for (int i = 0; i < cb.n; ++i) s = fma((T)cb.c[i], cb.v[i][t], s);
-        d[t] = s;
-        xt[t] = x[t] + (T)a * s;
+    const long long n4 = n / 4, stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const T ta = (T)a;
+    for (long long q = t0; q < n4; q += stride) {
+        T s[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 4
+        for (int i = 0; i < cb.n; ++i) {
+            T v[4];
+            ld4(cb.v[i] + 4 * q, v);
+            const T ci = (T)cb.c[i];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s[k] = fma(ci, v[k], s[k]);
+        }
+        T xv[4], xn[4];
+        ld4(x + 4 * q, xv);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) xn[k] = xv[k] + ta * s[k];
+        st4(d + 4 * q, s);
+        st4(xt + 4 * q, xn);
+    }
+    if (t0 < n - 4 * n4) {
+        const long long e = 4 * n4 + t0;
+        T sv = T(0);
+        for (int i = 0; i < cb.n; ++i) sv = fma((T)cb.c[i], cb.v[i][e], sv);
+        d[e] = sv;
+        xt[e] = x[e] + ta * sv;
     }
 }
 
@@ -98,17 +147,38 @@ struct Acc<float> {
     __device__ double value() const { return dot2_value(a); }
 };
 
+// CTA total of an accumulator (thread 0): FP64 tree for double, the
+// compensated FP32 tree for float.
+__device__ __forceinline__ double acc_total(const Acc<double> &a, double *red) { return block_total(a.value(), red); }
+__device__ __forceinline__ double acc_total(const Acc<float> &a, double *red)
+{
+    return dot2_block_sum(a.a, reinterpret_cast<Dot2 *>(red));
+}
+
 // xt = x + a d
 template <typename T>
 __global__ void k_trial(const T *__restrict__ x, const T *__restrict__ d, T *__restrict__ xt, double a, long long n)
 {
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x)
-        xt[t] = x[t] + (T)a * d[t];
+    const long long n4 = n / 4, stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const T ta = (T)a;
+    for (long long q = t0; q < n4; q += stride) {
+        T xv[4], dv[4];
+        ld4(x + 4 * q, xv);
+        ld4(d + 4 * q, dv);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) xv[k] = xv[k] + ta * dv[k];
+        st4(xt + 4 * q, xv);
+    }
+    if (t0 < n - 4 * n4) {
+        const long long e = 4 * n4 + t0;
+        xt[e] = x[e] + ta * d[e];
+    }
 }
 
 // s = xt - x, y = gt - g (stored), and per-CTA partials of
 // s.s, s.y, y.y, gt.s, gt.y, gt.gt at part[k * gridDim.x + blockIdx.x].
+// Grid-stride over quads; the last CTA also takes the n % 4 tail.
 template <typename T>
 __global__ void k_pair(const T *__restrict__ x, const T *__restrict__ xt, const T *__restrict__ g,
                        const T *__restrict__ gt, T *__restrict__ s_out, T *__restrict__ y_out, long long n,
@@ -116,22 +186,40 @@ __global__ void k_pair(const T *__restrict__ x, const T *__restrict__ xt, const 
 {
     __shared__ double red[32];
     Acc<T> acc[6];
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x) {
-        const T s = xt[t] - x[t], y = gt[t] - g[t];
-        const T gn = gt[t];
-        s_out[t] = s;
-        y_out[t] = y;
+    auto one = [&](T s, T y, T gn) {
         acc[0].add(s, s);
         acc[1].add(s, y);
         acc[2].add(y, y);
         acc[3].add(gn, s);
         acc[4].add(gn, y);
         acc[5].add(gn, gn);
+    };
+    const long long n4 = n / 4, stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
+        T xv[4], xtv[4], gv[4], gtv[4], sv[4], yv[4];
+        ld4(x + 4 * q, xv);
+        ld4(xt + 4 * q, xtv);
+        ld4(g + 4 * q, gv);
+        ld4(gt + 4 * q, gtv);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            sv[k] = xtv[k] - xv[k];
+            yv[k] = gtv[k] - gv[k];
+            one(sv[k], yv[k], gtv[k]);
+        }
+        st4(s_out + 4 * q, sv);
+        st4(y_out + 4 * q, yv);
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x < n % 4) {
+        const long long e = n - n % 4 + threadIdx.x;
+        const T sv = xt[e] - x[e], yv = gt[e] - g[e];
+        s_out[e] = sv;
+        y_out[e] = yv;
+        one(sv, yv, gt[e]);
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        const double v = block_total(acc[k].value(), red);
+        const double v = acc_total(acc[k], red);
         if (threadIdx.x == 0) part[k * gridDim.x + blockIdx.x] = v;
     }
 }
@@ -144,28 +232,55 @@ struct Slots {
     const T *Y[kMaxM];
 };
 
+// CTA (b, p) takes stored pairs j = 2p and 2p + 1 (when it exists), so that
+// s, y and gt are read once per two pairs; grid-stride over quads.
+// Partials at part[(j * 6 + k) * gridDim.x + b].
 template <typename T>
-__global__ void k_cross(const __grid_constant__ Slots<T> sl, const T *__restrict__ s, const T *__restrict__ y,
-                        const T *__restrict__ gt, long long n, double *__restrict__ part)
+__global__ void k_cross(const __grid_constant__ Slots<T> sl, int nu, const T *__restrict__ s,
+                        const T *__restrict__ y, const T *__restrict__ gt, long long n, double *__restrict__ part)
 {
     __shared__ double red[32];
-    const T *Sj = sl.S[blockIdx.y], *Yj = sl.Y[blockIdx.y];
-    Acc<T> acc[6];
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x) {
-        const T a = Sj[t], b = Yj[t];
-        const T sv = s[t], yv = y[t], gv = gt[t];
-        acc[0].add(sv, a);
-        acc[1].add(sv, b);
-        acc[2].add(yv, a);
-        acc[3].add(yv, b);
-        acc[4].add(gv, a);
-        acc[5].add(gv, b);
+    const int j0 = 2 * blockIdx.y;
+    const bool two = j0 + 1 < nu;
+    const T *S0 = sl.S[j0], *Y0 = sl.Y[j0];
+    const T *S1 = two ? sl.S[j0 + 1] : S0, *Y1 = two ? sl.Y[j0 + 1] : Y0;
+    Acc<T> acc[12];
+    auto one = [&](Acc<T> *a, T u, T w, T sv, T yv, T gv) {
+        a[0].add(sv, u);
+        a[1].add(sv, w);
+        a[2].add(yv, u);
+        a[3].add(yv, w);
+        a[4].add(gv, u);
+        a[5].add(gv, w);
+    };
+    const long long n4 = n / 4, stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
+        T sv[4], yv[4], gv[4], a0[4], b0[4];
+        ld4(s + 4 * q, sv);
+        ld4(y + 4 * q, yv);
+        ld4(gt + 4 * q, gv);
+        ld4(S0 + 4 * q, a0);
+        ld4(Y0 + 4 * q, b0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) one(acc, a0[k], b0[k], sv[k], yv[k], gv[k]);
+        if (two) {
+            T a1[4], b1[4];
+            ld4(S1 + 4 * q, a1);
+            ld4(Y1 + 4 * q, b1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) one(acc + 6, a1[k], b1[k], sv[k], yv[k], gv[k]);
+        }
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x < n % 4) {
+        const long long e = n - n % 4 + threadIdx.x;
+        one(acc, S0[e], Y0[e], s[e], y[e], gt[e]);
+        if (two) one(acc + 6, S1[e], Y1[e], s[e], y[e], gt[e]);
     }
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const double v = block_total(acc[k].value(), red);
-        if (threadIdx.x == 0) part[((size_t)blockIdx.y * 6 + k) * gridDim.x + blockIdx.x] = v;
+    for (int k = 0; k < 12; ++k) {
+        if (k >= 6 && !two) break;               // uniform across the CTA
+        const double v = acc_total(acc[k], red);
+        if (threadIdx.x == 0) part[((size_t)j0 * 6 + k) * gridDim.x + blockIdx.x] = v;
     }
 }
 
@@ -302,8 +417,8 @@ static tt_status accept_step(tt_lbfgs *st)
     if (nu > 0) {
         Slots<T> sl;
         for (int u = 0; u < nu; ++u) { sl.S[u] = (const T *)st->S[used[u]]; sl.Y[u] = (const T *)st->Y[used[u]]; }
-        k_cross<T><<<dim3(kPairBlocks, nu), 256, 0, h->stream>>>(sl, (const T *)st->ss, (const T *)st->ys,
-                                                               (const T *)st->gt, st->n, st->part + 6 * kPairBlocks);
+        k_cross<T><<<dim3(kPairBlocks, (nu + 1) / 2), 256, 0, h->stream>>>(
+            sl, nu, (const T *)st->ss, (const T *)st->ys, (const T *)st->gt, st->n, st->part + 6 * kPairBlocks);
     }
     const int rows = 6 + 6 * nu;
     k_rows<<<rows, 256, 0, h->stream>>>(st->part, kPairBlocks, st->dots);

@@ -128,17 +128,17 @@ __global__ void k_dot_partial(const T *__restrict__ x, const T *__restrict__ y, 
     __shared__ double red[32];
     double v = 0.0;
     if constexpr (std::is_same<T, float>::value) {
-        Dot2 a = {0.f, 0.f};                   // compensated FP32 per thread, FP64 across threads
+        Dot2 a = {0.f, 0.f};                   // compensated FP32 per thread and across the CTA
         for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
              t += (long long)gridDim.x * blockDim.x)
             dot2_add(a, x[t], y[t]);
-        v = dot2_value(a);
+        v = dot2_block_sum(a, reinterpret_cast<Dot2 *>(red));
     } else {
         for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
              t += (long long)gridDim.x * blockDim.x)
             v = fma(x[t], y[t], v);
+        v = block_sum(v, red);
     }
-    v = block_sum(v, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = v;
 }
 

@@ -13,7 +13,7 @@ __global__ void k_l2(const T *__restrict__ c, long long n, T *__restrict__ grad,
 {
     __shared__ double red[32];
     double v = 0.0;
-    Dot2 a = {0.f, 0.f};           // float: compensated FP32 per thread, FP64 across threads
+    Dot2 a = {0.f, 0.f};           // float: compensated FP32 per thread and across the CTA
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {
         const T x = c[t];
@@ -21,8 +21,8 @@ __global__ void k_l2(const T *__restrict__ c, long long n, T *__restrict__ grad,
         else v = fma(x, x, v);
         if (grad) grad[t] = T(2) * x;
     }
-    if constexpr (std::is_same<T, float>::value) v = dot2_value(a);
-    v = block_sum(v, red);
+    if constexpr (std::is_same<T, float>::value) v = dot2_block_sum(a, reinterpret_cast<Dot2 *>(red));
+    else v = block_sum(v, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = v;
 }
 
@@ -60,6 +60,7 @@ __global__ void k_tv_huber(const T *__restrict__ c, int nx, int ny, int nz, int 
     const long long n = (long long)nx * ny * nz * K;
     const T inv_delta = T(1) / delta;
     double v = 0.0;
+    Dot2 a = {0.f, 0.f};           // float: compensated FP32 sum of H
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t % K);
@@ -67,7 +68,8 @@ __global__ void k_tv_huber(const T *__restrict__ c, int nx, int ny, int nz, int 
         const int z = (int)(vox % nz), y = (int)((vox / nz) % ny), x = (int)(vox / ((long long)nz * ny));
         T g[3], w, H;
         tv_point<T>(c, x, y, z, nx, ny, nz, K, i, inv_delta, delta, g, w, H);
-        v += (double)H;
+        if constexpr (std::is_same<T, float>::value) dot2_add1(a, H);
+        else v += H;
         if (grad) {
             T gr = -w * (g[0] + g[1] + g[2]);
             T gm[3], wm, Hm;
@@ -77,7 +79,8 @@ __global__ void k_tv_huber(const T *__restrict__ c, int nx, int ny, int nz, int 
             grad[t] = gr;
         }
     }
-    v = block_sum(v, red);
+    if constexpr (std::is_same<T, float>::value) v = dot2_block_sum(a, reinterpret_cast<Dot2 *>(red));
+    else v = block_sum(v, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = v;
 }
 
