@@ -46,3 +46,26 @@ def test_profile_counts_and_times_every_launch():
     h.profile_reset()
     assert all(v == (0.0, 0) for v in h.profile_read().values())
     h.close()
+
+
+def test_profile_chain_over_several_adjoint_launches():
+    """300 projections: the adjoint runs as two launches (256 projections per
+    parameter block), all four launches of an evaluation sharing boundary
+    events; every launch is still counted and timed, and the results are
+    those of an unprofiled evaluation."""
+    st = synth.small_setup(n=(7, 6, 9), nj=8, nk=7, ell_max=4, n_proj=300, n_seg=5, seed=41)
+    h = tt.Handle(st, "f32")
+    c = torch.as_tensor(synth.random_volume(st, 42), dtype=torch.float32, device="cuda")
+    I = torch.as_tensor(synth.random_data(st, 43), dtype=torch.float32, device="cuda")
+    loss0, g0 = h.gradient_residual(c, I)
+    h.profile(True)
+    h.profile_reset()
+    for _ in range(50):
+        loss, g = h.gradient_residual(c, I)
+    p = h.profile_read()
+    h.profile(False)
+    assert p["pack"][1] == 50 and p["forward"][1] == 50 and p["adjoint"][1] == 100
+    assert all(p[k][0] > 0 for k in ("pack", "forward", "adjoint"))
+    assert loss == loss0
+    torch.testing.assert_close(g, g0, rtol=0, atol=0)
+    h.close()
