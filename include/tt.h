@@ -204,7 +204,7 @@ tt_status tt_tv_huber_f64(tt_handle *h, const double *c_dev, double delta, doubl
  * two loops run on the FP64 Gram matrix of the stored pairs and the gradient
  * (the same recursion in exact arithmetic; three vector kernels per
  * iteration); dot products of float vectors use compensated FP32 (Dot2)
- * accumulation per thread and FP64 across threads.  I_dev / W_dev (W may be NULL) are
+ * accumulation within a CTA and FP64 across CTAs.  I_dev / W_dev (W may be NULL) are
  * referenced, not copied: keep them alive and unchanged while the state
  * exists.  tt_lbfgs_create evaluates the loss and gradient at c0_dev. */
 tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0_dev, const void *I_dev,

@@ -14,7 +14,7 @@
 // new gradient with the stored pairs.  The recursion itself -- the same
 // arithmetic as the two loops, in exact arithmetic -- costs O(m^2) on the
 // host.  Dot products of float vectors use compensated FP32 accumulation
-// (Dot2) per thread and FP64 across threads; double vectors use FP64.
+// (Dot2) within a CTA and FP64 across CTAs; double vectors use FP64.
 #include <algorithm>
 #include <cmath>
 #include <utility>
