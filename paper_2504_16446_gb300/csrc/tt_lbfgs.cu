@@ -398,17 +398,24 @@ static tt_status enqueue_trial(tt_lbfgs *st, double a)
     return TT_OK;
 }
 
-// Accepted step: new pair into scratch, its dot products and those of the
-// new gradient with every stored pair, one read back.  Then the Gram matrix
-// is updated, the pair stored if the curvature condition holds, and x, g
-// advance.
+// Stored pair slots, newest first.
+static std::vector<int> used_slots(const tt_lbfgs *st)
+{
+    std::vector<int> used;
+    for (int t = 0; t < st->count; ++t) used.push_back((st->head - t + st->m) % st->m);
+    return used;
+}
+
+// For a trial point: its pair s = xt - x, y = gt - g into scratch, the six
+// dot products of the pair and gt, and those of s, y, gt with every stored
+// pair; their copy to the host is enqueued behind them, so the stream
+// synchronisation that reads the trial loss also delivers them.  (Enqueued
+// before the Armijo test is known: a rejected trial wastes these kernels,
+// an accepted one -- nearly every first trial -- saves a synchronisation.)
 template <typename T>
-static tt_status accept_step(tt_lbfgs *st)
+static tt_status enqueue_pair_dots(tt_lbfgs *st, const std::vector<int> &used)
 {
     tt_handle *h = st->h;
-    const int m = st->m;
-    std::vector<int> used;
-    for (int t = 0; t < st->count; ++t) used.push_back((st->head - t + m) % m);
     const int nu = (int)used.size();
     cudaEvent_t ev;
     prof_begin(h, TT_KSLOT_VECTOR, &ev);
@@ -427,7 +434,16 @@ static tt_status accept_step(tt_lbfgs *st)
     TT_CUDA(e, "lbfgs pair dots");
     TT_CUDA(cudaMemcpyAsync(st->pinned, st->dots, sizeof(double) * rows, cudaMemcpyDeviceToHost, h->stream),
             "lbfgs dots copy");
-    TT_CUDA(cudaStreamSynchronize(h->stream), "stream synchronize");
+    return TT_OK;
+}
+
+// Accepted trial (its dot products have arrived in st->pinned): the Gram
+// matrix is updated, the pair stored if the curvature condition holds, and
+// x, g advance.
+static void finish_accept(tt_lbfgs *st, const std::vector<int> &used)
+{
+    const int m = st->m;
+    const int nu = (int)used.size();
     const double *P = st->pinned;
     const double ss = P[0], sy = P[1], yy = P[2], gs = P[3], gy = P[4], gg = P[5];
     const int ig = st->ig();
@@ -462,8 +478,8 @@ static tt_status accept_step(tt_lbfgs *st)
     }
     std::swap(st->x, st->xt);
     std::swap(st->g, st->gt);
-    return TT_OK;
 }
+
 
 template <typename T>
 static tt_status lbfgs_step(tt_lbfgs *st, double *loss_out, int *n_evals_out)
@@ -496,6 +512,7 @@ static tt_status lbfgs_step(tt_lbfgs *st, double *loss_out, int *n_evals_out)
     double a = step0;
     tt_status s = enqueue_direction<T>(st, c, a);
     if (s != TT_OK) return s;
+    const std::vector<int> used = used_slots(st);
     for (int ne = 1; ne <= max_evals; ++ne) {
         if (ne > 1) {
             s = enqueue_trial<T>(st, a);
@@ -503,12 +520,13 @@ static tt_status lbfgs_step(tt_lbfgs *st, double *loss_out, int *n_evals_out)
         }
         s = tt_grad_enqueue<T>(h, (const T *)st->xt, (const T *)st->I, (const T *)st->W, (T *)st->gt);
         if (s != TT_OK) return s;
+        s = enqueue_pair_dots<T>(st, used);
+        if (s != TT_OK) return s;
         double ft = 0.0;
-        s = tt_read_loss(h, &ft);
+        s = tt_read_loss(h, &ft);                        // synchronises: the dots are in too
         if (s != TT_OK && s != TT_NONFINITE) return s;
         if (s == TT_OK && ft <= st->f + c1 * a * gd) {
-            s = accept_step<T>(st);
-            if (s != TT_OK) return s;
+            finish_accept(st, used);
             st->f = ft;
             if (loss_out) *loss_out = ft;
             if (n_evals_out) *n_evals_out = ne;

@@ -42,6 +42,33 @@ def test_lbfgs_fp64_matches_oracle_step_by_step():
     assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
 
 
+def test_lbfgs_fp64_rejected_trials_match_the_oracle():
+    """A solution of norm ~0.1 against a first step of length 1: the line
+    search rejects three trials before accepting one.  The device enqueues
+    each trial's pair and dot products before the Armijo test; a rejected
+    trial's must leave no trace in the Gram matrix."""
+    st = synth.small_setup(n=(7, 8, 6), nj=10, nk=10, ell_max=2, n_proj=10, n_seg=8, seed=5)
+    g = oracle_geometry(st)
+    I = synth.gaussian_noise(oracle.forward(g, synth.random_volume(st, 6) * 1e-2), 0.01, seed=7)
+    W = synth.random_weights(st, seed=8)
+    B = oracle.basis_matrix(g)
+    fg = lambda x: oracle.gradient_residual(g, x.reshape(st.volume_shape), I, W, B)
+    ref = OracleLBFGS(fg, np.zeros(int(np.prod(st.volume_shape))), m=3)
+    h = tt.Handle(st, "f64")
+    opt = tt.LBFGS(h, torch.zeros(st.volume_shape, dtype=torch.float64, device="cuda"),
+                   torch.as_tensor(I, device="cuda"), torch.as_tensor(W, device="cuda"), m=3)
+    evals = []
+    for it in range(12):
+        f_ref, ne_ref, st_ref = ref.step()
+        f, ne, status = opt.step()
+        evals.append(ne)
+        assert status == st_ref == 0 and ne == ne_ref, it
+        assert abs(f - f_ref) <= 1e-9 * f_ref, (it, f, f_ref)
+    assert evals[0] == 4
+    x = opt.get()[0].cpu().numpy().ravel()
+    assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+
+
 @pytest.mark.parametrize("m", [1, 3])
 def test_lbfgs_fp64_short_memory_wraps_like_the_oracle(m):
     """With m = 1 or 3 the pair store wraps around within a few iterations:
