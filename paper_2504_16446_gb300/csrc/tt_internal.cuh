@@ -29,6 +29,10 @@ __host__ __device__ constexpr int num_coeffs(int L) { return (L + 1) * (L + 2) /
 // Voxels a lane group of the adjoint owns: all LG while a lane's accumulators
 // (V * KP / LG) fit in 16 registers' worth of channels, else as many as keep
 // them within 24 (one for the largest K).
+// Lane groups of an adjoint warp along z, the rest side by side in x: eight
+// (a warp covers 8 z x 32 / (8 LG) x-columns of V voxels each), all 32 for
+// one-lane groups (measured 3% faster for those than 8 z x 4 x).
+__host__ __device__ constexpr int adjoint_gz(int LG) { return LG == 1 ? 32 : (32 / LG < 8 ? 32 / LG : 8); }
 __host__ __device__ constexpr int adjoint_voxels(int KP, int LG)
 {
     return KP / LG <= 4 ? LG : ((24 / (KP / LG)) < 1 ? 1 : ((24 / (KP / LG)) > LG ? LG : 24 / (KP / LG)));

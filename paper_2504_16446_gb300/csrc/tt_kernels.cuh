@@ -583,22 +583,26 @@ k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const S *__restrict__ 
         if (threadIdx.x == 0) loss_out[0] = v;
     }
     constexpr int CPL = KP / LG;
-    // A warp's 32/LG lane groups take consecutive z; a group owns V voxels,
-    // source v being (32/LG) * v further along z, so that the rows the warp
-    // reads for one broadcast source are rays of neighbouring voxels.  Lane
-    // q computes the candidate geometry of voxel q % V (V <= LG; with V < LG
+    // A warp's 32/LG lane groups take GZ consecutive z (times GX columns in
+    // x); a group owns V voxels adjacent in x, so that the rows the warp
+    // reads for one broadcast source are rays of neighbouring voxels and a
+    // CTA covers a compact block (8 x 4 x 8 voxels for K = 15: z tiles of 8
+    // waste little on volumes whose size is no multiple of 32).  Lane q
+    // computes the candidate geometry of voxel q % V (V <= LG; with V < LG
     // lanes repeat a voxel's geometry so that the accumulators, V * CPL per
     // lane, stay in registers for large K).
     constexpr int GPW = 32 / LG;                   // lane groups per warp
-    constexpr int BZ = GPW * V, BY = 4, BX = (kThreads / 32) / BY;
+    constexpr int GZ = adjoint_gz(LG), GX = GPW / GZ, BY = 4, BX = (kThreads / 32) / BY;
 
     const int b = blockIdx.x;
     const int bz = b % tz, by = (b / tz) % ty, bx = b / (tz * ty);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = lane / LG, q = lane % LG;
-    const int x = bx * BX + warp / BY, y = by * BY + warp % BY;
-    const int z0 = bz * BZ + gw;                   // voxel of source v is z0 + GPW * v
-    const int z = z0 + GPW * (q % V);
+    const int xw = (bx * BX + warp / BY) * (GX * V);   // first x of the warp
+    const int x0 = xw + (gw / GZ) * V;             // voxel of source v is (x0 + v, y, z)
+    const int y = by * BY + warp % BY;
+    const int z = bz * GZ + gw % GZ;
+    const int x = x0 + q % V;
     const bool valid = (x < nx) && (y < ny) && (z < nz);
     const T fx = (T)x, fy = (T)y, fz = (T)z;
 
@@ -615,7 +619,7 @@ k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const S *__restrict__ 
     int *rb = s_r + (kSmem ? (threadIdx.x / LG) * 12 : 0);
 
     // Warps whose voxels all lie outside the volume skip the loop as a whole.
-    const bool group_live = (x < nx) && (y < ny) && (bz * BZ < nz);
+    const bool group_live = (xw < nx) && (y < ny) && (bz * GZ < nz);
     if (group_live) {
         for (int si = 0; si < ns; ++si) {
             const AdjProj<T> &c = P.p[si];
@@ -650,9 +654,9 @@ k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const S *__restrict__ 
     // lane q writes channel chunk q of the group's V voxels
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        const int zv = z0 + GPW * v;
-        if (!(x < nx && y < ny && zv < nz)) continue;
-        const long long vox = ((long long)x * ny + y) * nz + zv;
+        const int xv = x0 + v;
+        if (!(xv < nx && y < ny && z < nz)) continue;
+        const long long vox = ((long long)xv * ny + y) * nz + z;
         if (accumulate) {
             const T *prev = gpad + vox * KP + q * CPL;
 #pragma unroll
@@ -726,8 +730,8 @@ cudaError_t launch_adjoint_L(tt_handle *h, T *g, bool reduce_loss)
     // For K <= 8 a single lane owns a voxel and reads its whole (32-byte) G
     // row: no candidate exchange, measured 7% faster than two-lane groups.
     constexpr int K = num_coeffs(L), KP = padded_k(K), LG = K <= 8 ? 1 : lane_group(K), V = adjoint_voxels(KP, LG);
-    constexpr int BZ = (32 / LG) * V, BY = 4, BX = (kThreads / 32) / BY;
-    const int tx = (h->N[0] + BX - 1) / BX, ty = (h->N[1] + BY - 1) / BY, tz = (h->N[2] + BZ - 1) / BZ;
+    constexpr int GZ = adjoint_gz(LG), BXT = (kThreads / 32 / 4) * (32 / LG / GZ) * V, BY = 4;
+    const int tx = (h->N[0] + BXT - 1) / BXT, ty = (h->N[1] + BY - 1) / BY, tz = (h->N[2] + GZ - 1) / GZ;
     const std::vector<AdjParams<T>> &chunks = adj_params<T>(h);
     const T *G = (const T *)h->G;           // G is kept in T for every storage type
     cudaError_t e = cudaSuccess;
