@@ -425,8 +425,8 @@ __device__ __forceinline__ int sel3(int x, int y, int z, int axis)
 // point whose true weight is positive but within FP rounding of zero may be
 // left out: its contribution is below the rounding of the others.
 //
-// Work split: a lane group of LG lanes owns V <= LG voxels (consecutive in
-// z).  Lane q does the candidate geometry for voxel q % V only, then the
+// Work split: a lane group of LG lanes owns V <= LG voxels (adjacent in
+// x).  Lane q does the candidate geometry for voxel q % V only, then the
 // group exchanges each candidate's weight and each column's first row --
 // through shared memory for FP32 (one 16-byte read gives a candidate's
 // weights for all sources; shuffles would take a load-store-unit wavefront
