@@ -319,10 +319,14 @@ tt_status tt_zonal_to_sh(int ell_max, long long n, const float *dirs_dev, const 
                          float *c_dev, void *stream);
 
 /* Kernel-time accounting.  When enabled, every kernel libtt launches on the
- * handle's stream is bracketed by CUDA events; tt_profile_read synchronises
- * and returns, for kernel class `slot`, the summed device time in ms and the
- * launch count since the last reset.  tt_launch_count counts all kernel
- * launches of the handle since creation (always on). */
+ * handle's stream is bracketed by CUDA events (the launches of one gradient
+ * evaluation, enqueued back to back, share their boundary events, so a
+ * launch's time includes the gap before the next one); tt_profile_enable
+ * pre-creates the events, and completed pairs are recycled as later launches
+ * are enqueued.  tt_profile_read synchronises and returns, for kernel class
+ * `slot`, the summed device time in ms and the launch count since the last
+ * reset.  tt_launch_count counts all kernel launches of the handle since
+ * creation (always on). */
 enum {
     TT_KSLOT_PACK = 0, TT_KSLOT_FORWARD = 1, TT_KSLOT_BACKCONTRACT = 2, TT_KSLOT_ADJOINT = 3,
     TT_KSLOT_UNPACK = 4, TT_KSLOT_REDUCE = 5, TT_KSLOT_BASIS = 6, TT_KSLOT_VECTOR = 7,
