@@ -17,6 +17,8 @@
 // (Dot2) within a CTA and FP64 across CTAs; double vectors use FP64.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
+#include <cstring>
 #include <utility>
 #include <vector>
 
@@ -552,16 +554,11 @@ static tt_status initial_gram(tt_lbfgs *st)
     return TT_OK;
 }
 
-extern "C" {
-
-tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0, const void *I, const void *W, tt_lbfgs **out)
+// Memory of a state: every vector in one slab of 256-byte aligned pitches
+// (x, g, d, xt, gt, scratch pair, m stored pairs), the dot-product partials
+// and their pinned host copy.  Counters and the Gram matrix start empty.
+static tt_status alloc_state(tt_handle *h, int m, const void *I, const void *W, tt_lbfgs **out)
 {
-    if (!out) { set_error("tt_lbfgs_create: out must not be NULL"); return TT_INVALID_ARG; }
-    *out = nullptr;
-    if (!h || !c0 || !I || m < 1 || m > kMaxM) {
-        set_error("tt_lbfgs_create: need a handle, c0, I and 1 <= m <= 64");
-        return TT_INVALID_ARG;
-    }
     tt_lbfgs *st = new tt_lbfgs();
     st->h = h;
     st->m = m;
@@ -571,9 +568,9 @@ tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0, const void *I, co
     st->I = I;
     st->W = W;
     const size_t bytes = h->esize() * st->n;
-    const size_t pitch = (bytes + 255) / 256 * 256;     // 256-byte aligned vectors in one slab
+    const size_t pitch = (bytes + 255) / 256 * 256;
     cudaError_t e = cudaMalloc(&st->slab, pitch * (7 + 2 * (size_t)m));
-    if (e != cudaSuccess) { free_state(st); return cuda_fail(e, "tt_lbfgs_create: cudaMalloc"); }
+    if (e != cudaSuccess) { free_state(st); return cuda_fail(e, "L-BFGS state: cudaMalloc"); }
     char *base = (char *)st->slab;
     void **bufs[] = {&st->x, &st->g, &st->d, &st->xt, &st->gt, &st->ss, &st->ys};
     for (void **b : bufs) { *b = base; base += pitch; }
@@ -587,15 +584,132 @@ tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0, const void *I, co
     e = cudaMalloc(&st->part, sizeof(double) * std::max<size_t>(rows * kPairBlocks, kDotBlocks));
     if (e == cudaSuccess) e = cudaMalloc(&st->dots, sizeof(double) * rows);
     if (e == cudaSuccess) e = cudaMallocHost(&st->pinned, sizeof(double) * rows);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(st->x, c0, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) { free_state(st); return cuda_fail(e, "L-BFGS state"); }
+    *out = st;
+    return TT_OK;
+}
+
+// Checkpoint layout: this header, the Gram matrix (nb x nb FP64), then x, g
+// and the stored pairs S, Y from the newest to the oldest, each n elements
+// of the handle's element type.
+static const char kCheckpointMagic[8] = {'T', 'T', 'L', 'B', 'F', 'G', 'S', '1'};
+struct CheckpointHeader {
+    char magic[8];
+    int32_t m, count, head, esize;
+    int64_t n;
+    double f;
+    int32_t nb, reserved;
+};
+
+static size_t checkpoint_bytes(int nb, long long n, size_t esize, int count)
+{
+    return sizeof(CheckpointHeader) + sizeof(double) * (size_t)nb * nb + esize * (size_t)n * (2 + 2 * (size_t)count);
+}
+
+extern "C" {
+
+tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0, const void *I, const void *W, tt_lbfgs **out)
+{
+    if (!out) { set_error("tt_lbfgs_create: out must not be NULL"); return TT_INVALID_ARG; }
+    *out = nullptr;
+    if (!h || !c0 || !I || m < 1 || m > kMaxM) {
+        set_error("tt_lbfgs_create: need a handle, c0, I and 1 <= m <= 64");
+        return TT_INVALID_ARG;
+    }
+    tt_lbfgs *st = nullptr;
+    tt_status s = alloc_state(h, m, I, W, &st);
+    if (s != TT_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(st->x, c0, h->esize() * st->n, cudaMemcpyDeviceToDevice, h->stream);
     if (e != cudaSuccess) { free_state(st); return cuda_fail(e, "tt_lbfgs_create"); }
-    tt_status s = (h->prec != TT_F64)
-                      ? tt_grad_enqueue<float>(h, (const float *)st->x, (const float *)I, (const float *)W, (float *)st->g)
-                      : tt_grad_enqueue<double>(h, (const double *)st->x, (const double *)I, (const double *)W,
-                                                (double *)st->g);
+    s = (h->prec != TT_F64)
+            ? tt_grad_enqueue<float>(h, (const float *)st->x, (const float *)I, (const float *)W, (float *)st->g)
+            : tt_grad_enqueue<double>(h, (const double *)st->x, (const double *)I, (const double *)W, (double *)st->g);
     if (s == TT_OK) s = tt_read_loss(h, &st->f);
     if (s == TT_OK) s = (h->prec != TT_F64) ? initial_gram<float>(st) : initial_gram<double>(st);
     if (s != TT_OK) { free_state(st); return s; }
+    *out = st;
+    return TT_OK;
+}
+
+long long tt_lbfgs_checkpoint_bytes(const tt_lbfgs *st)
+{
+    if (!st) return 0;
+    return (long long)checkpoint_bytes(st->nb, st->n, st->h ? st->h->esize() : 0, st->count);
+}
+
+tt_status tt_lbfgs_save(tt_handle *h, const tt_lbfgs *st, void *buf, long long bytes)
+{
+    if (!h || !st || st->h != h) { set_error("tt_lbfgs_save: state does not belong to this handle"); return TT_INVALID_ARG; }
+    const size_t es = h->esize(), need = checkpoint_bytes(st->nb, st->n, es, st->count);
+    if (!buf || bytes < (long long)need) {
+        set_error("tt_lbfgs_save: buf must hold tt_lbfgs_checkpoint_bytes(st) bytes");
+        return TT_INVALID_ARG;
+    }
+    CheckpointHeader hd{};
+    std::memcpy(hd.magic, kCheckpointMagic, sizeof hd.magic);
+    hd.m = st->m; hd.count = st->count; hd.head = st->head; hd.esize = (int)es;
+    hd.n = st->n; hd.f = st->f; hd.nb = st->nb;
+    char *p = (char *)buf;
+    std::memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    std::memcpy(p, st->gram.data(), sizeof(double) * st->gram.size());
+    p += sizeof(double) * st->gram.size();
+    const size_t vb = es * st->n;
+    std::vector<const void *> src = {st->x, st->g};
+    for (int t = 0; t < st->count; ++t) {
+        const int k = (st->head - t + st->m) % st->m;
+        src.push_back(st->S[k]);
+        src.push_back(st->Y[k]);
+    }
+    for (const void *v : src) {
+        TT_CUDA(cudaMemcpyAsync(p, v, vb, cudaMemcpyDeviceToHost, h->stream), "tt_lbfgs_save: copy");
+        p += vb;
+    }
+    TT_CUDA(cudaStreamSynchronize(h->stream), "tt_lbfgs_save: synchronize");
+    return TT_OK;
+}
+
+tt_status tt_lbfgs_restore(tt_handle *h, const void *buf, long long bytes, const void *I, const void *W, tt_lbfgs **out)
+{
+    if (!out) { set_error("tt_lbfgs_restore: out must not be NULL"); return TT_INVALID_ARG; }
+    *out = nullptr;
+    if (!h || !buf || !I || bytes < (long long)sizeof(CheckpointHeader)) {
+        set_error("tt_lbfgs_restore: need a handle, a checkpoint and I");
+        return TT_INVALID_ARG;
+    }
+    CheckpointHeader hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    const size_t es = h->esize();
+    if (std::memcmp(hd.magic, kCheckpointMagic, sizeof hd.magic) != 0 || hd.m < 1 || hd.m > kMaxM ||
+        hd.nb != 2 * hd.m + 1 || hd.count < 0 || hd.count > hd.m || (hd.count > 0 && (hd.head < 0 || hd.head >= hd.m)) ||
+        hd.n != h->nvox() * h->K || hd.esize != (int)es ||
+        bytes != (long long)checkpoint_bytes(hd.nb, hd.n, es, hd.count)) {
+        set_error("tt_lbfgs_restore: not a checkpoint of an L-BFGS state of this problem and precision");
+        return TT_INVALID_ARG;
+    }
+    tt_lbfgs *st = nullptr;
+    tt_status s = alloc_state(h, hd.m, I, W, &st);
+    if (s != TT_OK) return s;
+    st->count = hd.count;
+    st->head = hd.head;
+    st->f = hd.f;
+    const char *p = (const char *)buf + sizeof hd;
+    std::memcpy(st->gram.data(), p, sizeof(double) * st->gram.size());
+    p += sizeof(double) * st->gram.size();
+    const size_t vb = es * st->n;
+    std::vector<void *> dst = {st->x, st->g};
+    for (int t = 0; t < st->count; ++t) {
+        const int k = (st->head - t + st->m) % st->m;
+        dst.push_back(st->S[k]);
+        dst.push_back(st->Y[k]);
+    }
+    cudaError_t e = cudaSuccess;
+    for (void *v : dst) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(v, p, vb, cudaMemcpyHostToDevice, h->stream);
+        p += vb;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) { free_state(st); return cuda_fail(e, "tt_lbfgs_restore: copy"); }
     *out = st;
     return TT_OK;
 }

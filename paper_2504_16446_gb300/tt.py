@@ -85,6 +85,9 @@ SIGNATURES = {
     "tt_lbfgs_step": (ctypes.c_int, [_P, _P, _P, _D, ctypes.POINTER(ctypes.c_int)]),
     "tt_lbfgs_get": (ctypes.c_int, [_P, _P, _P, _P, _D]),
     "tt_lbfgs_destroy": (ctypes.c_int, [_P]),
+    "tt_lbfgs_checkpoint_bytes": (ctypes.c_longlong, [_P]),
+    "tt_lbfgs_save": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong]),
+    "tt_lbfgs_restore": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P, _P, ctypes.POINTER(_P)]),
     "tt_sirt_weights": (ctypes.c_int, [_P, _P, _P, _P]),
     "tt_sirt_weights_f64": (ctypes.c_int, [_P, _P, _P, _P]),
     "tt_mitra_create": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_P)]),
@@ -345,6 +348,33 @@ class LBFGS:
                "tt_lbfgs_create")
         self._st = st
         self.loss = self.get()[2]
+
+    def save(self) -> np.ndarray:
+        """Checkpoint of the state (iterate, gradient, stored pairs, Gram
+        matrix, counters, loss) as a host byte array (tt_lbfgs_save)."""
+        self.h._sync_stream()
+        n = int(self.h.lib.tt_lbfgs_checkpoint_bytes(self._st))
+        buf = np.empty(n, dtype=np.uint8)
+        _check(self.h.lib.tt_lbfgs_save(self.h._h, self._st, buf.ctypes.data_as(_P), n), "tt_lbfgs_save")
+        return buf
+
+    @classmethod
+    def restore(cls, handle: "Handle", buf: np.ndarray, I: torch.Tensor, W: torch.Tensor | None = None) -> "LBFGS":
+        """A state from a checkpoint of save() (tt_lbfgs_restore); I and W as
+        for the constructor."""
+        handle._sync_stream()
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        dt, ds = handle.dtype, handle.data_shape
+        st = _P()
+        _check(handle.lib.tt_lbfgs_restore(handle._h, buf.ctypes.data_as(_P), int(buf.size), _dptr(I, dt, ds, "I"),
+                                           None if W is None else _dptr(W, dt, ds, "W"), ctypes.byref(st)),
+               "tt_lbfgs_restore")
+        self = cls.__new__(cls)
+        self.h = handle
+        self._keep = (None, I, W)
+        self._st = st
+        self.loss = self.get()[2]
+        return self
 
     def step(self):
         """One iteration -> (loss, n_evals, status); raises on errors other than line-search failure."""

@@ -124,3 +124,40 @@ def test_lbfgs_state_buffers_start_from_recycled_nan_memory():
         f, ne, status = opt.step()
         assert status == tt.TT_OK and np.isfinite(f)
     assert f < 0.2 * f0
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_lbfgs_checkpoint_resume_continues_exactly(prec, tmp_path):
+    """Save after the pair store has wrapped (m = 4, 6 iterations), continue
+    the original for 5 iterations, restore the checkpoint (through a file)
+    into a new state and run the same 5: losses, evaluation counts and the
+    final iterate are bit-identical.  Checkpoints of another precision or a
+    truncated buffer are rejected."""
+    st, g, I = _problem(3, n=(9, 8, 7))
+    dt = torch.float32 if prec == "f32" else torch.float64
+    h = tt.Handle(st, prec)
+    Id = torch.as_tensor(I, device="cuda", dtype=dt)
+    a = tt.LBFGS(h, torch.zeros(st.volume_shape, dtype=dt, device="cuda"), Id, None, m=4)
+    for _ in range(6):
+        a.step()
+    ck = a.save()
+    loss_at_save = a.loss
+    path = tmp_path / "lbfgs.npy"
+    np.save(path, ck)
+    cont = [a.step()[:2] for _ in range(5)]
+    xa = a.get()[0]
+    b = tt.LBFGS.restore(h, np.load(path), Id)
+    assert b.loss == loss_at_save
+    assert [b.step()[:2] for _ in range(5)] == cont
+    assert torch.equal(b.get()[0], xa)
+    other = tt.Handle(st, "f64" if prec == "f32" else "f32")
+    with pytest.raises(tt.TTError):
+        tt.LBFGS.restore(other, ck, torch.as_tensor(I, device="cuda", dtype=other.dtype))
+    with pytest.raises(tt.TTError):
+        tt.LBFGS.restore(h, ck[:-8], Id)
+    bad = ck.copy()
+    bad[0] ^= 1
+    with pytest.raises(tt.TTError):
+        tt.LBFGS.restore(h, bad, Id)
+    a.close()
+    b.close()
