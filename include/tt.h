@@ -219,14 +219,21 @@ tt_status tt_lbfgs_step(tt_handle *h, tt_lbfgs *st, void *c_out_dev, double *los
 tt_status tt_lbfgs_get(tt_handle *h, tt_lbfgs *st, void *c_dev, void *g_dev, double *loss_host);
 /* Frees the state; valid before or after tt_destroy of its handle. */
 tt_status tt_lbfgs_destroy(tt_lbfgs *st);
+/* Counters of the state (any pointer may be NULL): accepted iterations,
+ * gradient evaluations including the one of tt_lbfgs_create, and the
+ * line-search step a of the last accepted iteration (x_new = x + a d; a = 1
+ * is the full quasi-Newton step; with no stored pairs d = -g and the search
+ * starts at a = 1/|g|). */
+tt_status tt_lbfgs_stats(const tt_lbfgs *st, long long *iterations, long long *evaluations, double *last_step);
 /* Checkpoint / resume of an L-BFGS state.  tt_lbfgs_checkpoint_bytes gives
  * the size of the state's checkpoint as it stands (it grows with the number
  * of stored pairs; 0 for NULL).  tt_lbfgs_save writes it into the host
  * buffer buf (at least that many bytes; caller-owned, any host memory) and
  * synchronises the handle's stream: a header (magic "TTLBFGS1", memory m,
- * stored pairs, newest slot, element size, n, loss), the FP64 Gram matrix,
- * then the iterate, the gradient and the stored pairs, newest first, as
- * n-element vectors of the handle's element type.  tt_lbfgs_restore creates
+ * stored pairs, newest slot, element size, n, loss, the counters of
+ * tt_lbfgs_stats), the FP64 Gram matrix, then the iterate, the gradient and
+ * the stored pairs, newest first, as n-element vectors of the handle's
+ * element type.  tt_lbfgs_restore creates
  * a state of handle h from such a buffer (bytes = its exact size); I_dev /
  * W_dev are not part of a checkpoint and are passed as to tt_lbfgs_create.
  * The restored state continues exactly as the saved one would have.

@@ -307,6 +307,8 @@ struct tt_lbfgs {
     std::vector<void *> S, Y;
     int count = 0, head = -1;     // stored pairs; slot of the newest
     double f = 0.0;
+    long long iterations = 0, evaluations = 1;   // accepted steps; gradient evaluations (creation's included)
+    double last_step = 0.0;       // line-search step of the last accepted iteration, along d
     const void *I = nullptr, *W = nullptr;
     // Gram matrix of b = (S_0..S_{m-1}, Y_0..Y_{m-1}, g), (2m+1)^2, FP64
     std::vector<double> gram;
@@ -526,10 +528,13 @@ static tt_status lbfgs_step(tt_lbfgs *st, double *loss_out, int *n_evals_out)
         if (s != TT_OK) return s;
         double ft = 0.0;
         s = tt_read_loss(h, &ft);                        // synchronises: the dots are in too
+        ++st->evaluations;
         if (s != TT_OK && s != TT_NONFINITE) return s;
         if (s == TT_OK && ft <= st->f + c1 * a * gd) {
             finish_accept(st, used);
             st->f = ft;
+            ++st->iterations;
+            st->last_step = a;
             if (loss_out) *loss_out = ft;
             if (n_evals_out) *n_evals_out = ne;
             return TT_OK;
@@ -599,6 +604,8 @@ struct CheckpointHeader {
     int64_t n;
     double f;
     int32_t nb, reserved;
+    int64_t iterations, evaluations;
+    double last_step;
 };
 
 static size_t checkpoint_bytes(int nb, long long n, size_t esize, int count)
@@ -631,6 +638,15 @@ tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0, const void *I, co
     return TT_OK;
 }
 
+tt_status tt_lbfgs_stats(const tt_lbfgs *st, long long *iterations, long long *evaluations, double *last_step)
+{
+    if (!st) { set_error("tt_lbfgs_stats: null state"); return TT_INVALID_ARG; }
+    if (iterations) *iterations = st->iterations;
+    if (evaluations) *evaluations = st->evaluations;
+    if (last_step) *last_step = st->last_step;
+    return TT_OK;
+}
+
 long long tt_lbfgs_checkpoint_bytes(const tt_lbfgs *st)
 {
     if (!st) return 0;
@@ -649,6 +665,7 @@ tt_status tt_lbfgs_save(tt_handle *h, const tt_lbfgs *st, void *buf, long long b
     std::memcpy(hd.magic, kCheckpointMagic, sizeof hd.magic);
     hd.m = st->m; hd.count = st->count; hd.head = st->head; hd.esize = (int)es;
     hd.n = st->n; hd.f = st->f; hd.nb = st->nb;
+    hd.iterations = st->iterations; hd.evaluations = st->evaluations; hd.last_step = st->last_step;
     char *p = (char *)buf;
     std::memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
@@ -693,6 +710,9 @@ tt_status tt_lbfgs_restore(tt_handle *h, const void *buf, long long bytes, const
     st->count = hd.count;
     st->head = hd.head;
     st->f = hd.f;
+    st->iterations = hd.iterations;
+    st->evaluations = hd.evaluations;
+    st->last_step = hd.last_step;
     const char *p = (const char *)buf + sizeof hd;
     std::memcpy(st->gram.data(), p, sizeof(double) * st->gram.size());
     p += sizeof(double) * st->gram.size();

@@ -86,6 +86,7 @@ SIGNATURES = {
     "tt_lbfgs_get": (ctypes.c_int, [_P, _P, _P, _P, _D]),
     "tt_lbfgs_destroy": (ctypes.c_int, [_P]),
     "tt_lbfgs_checkpoint_bytes": (ctypes.c_longlong, [_P]),
+    "tt_lbfgs_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _D]),
     "tt_lbfgs_save": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong]),
     "tt_lbfgs_restore": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P, _P, ctypes.POINTER(_P)]),
     "tt_sirt_weights": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -348,6 +349,22 @@ class LBFGS:
                "tt_lbfgs_create")
         self._st = st
         self.loss = self.get()[2]
+        self._start_log(I, W)
+
+    def _start_log(self, I, W):
+        """Per-iteration log: loss, gradient evaluations, line-search step and
+        the relative data residual sqrt(L / sum W I^2)."""
+        Id = I.double()
+        self._data_norm2 = float(torch.sum(Id * Id if W is None else W.double() * Id * Id))
+        self.history = []
+
+    def stats(self) -> dict:
+        """Accepted iterations, gradient evaluations (creation's included) and
+        the line-search step of the last iteration (tt_lbfgs_stats)."""
+        it, ev, a = ctypes.c_longlong(0), ctypes.c_longlong(0), ctypes.c_double(0.0)
+        _check(self.h.lib.tt_lbfgs_stats(self._st, ctypes.byref(it), ctypes.byref(ev), ctypes.byref(a)),
+               "tt_lbfgs_stats")
+        return {"iterations": it.value, "evaluations": ev.value, "last_step": a.value}
 
     def save(self) -> np.ndarray:
         """Checkpoint of the state (iterate, gradient, stored pairs, Gram
@@ -374,6 +391,7 @@ class LBFGS:
         self._keep = (None, I, W)
         self._st = st
         self.loss = self.get()[2]
+        self._start_log(I, W)
         return self
 
     def step(self):
@@ -385,6 +403,9 @@ class LBFGS:
         if st not in (TT_OK, TT_LINESEARCH_FAILED):
             _check(st, "tt_lbfgs_step")
         self.loss = loss.value
+        self.history.append({"loss": loss.value, "evals": ne.value, "step": self.stats()["last_step"],
+                             "relative_residual": (loss.value / self._data_norm2) ** 0.5
+                             if self._data_norm2 > 0 else float("nan"), "status": st})
         return loss.value, ne.value, st
 
     def get(self):

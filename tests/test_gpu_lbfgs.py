@@ -58,13 +58,23 @@ def test_lbfgs_fp64_rejected_trials_match_the_oracle():
     opt = tt.LBFGS(h, torch.zeros(st.volume_shape, dtype=torch.float64, device="cuda"),
                    torch.as_tensor(I, device="cuda"), torch.as_tensor(W, device="cuda"), m=3)
     evals = []
+    g0_norm = float(np.linalg.norm(ref.g))
     for it in range(12):
         f_ref, ne_ref, st_ref = ref.step()
         f, ne, status = opt.step()
         evals.append(ne)
         assert status == st_ref == 0 and ne == ne_ref, it
         assert abs(f - f_ref) <= 1e-9 * f_ref, (it, f, f_ref)
+        # the accepted step: halvings from 1/|g0| on the first iteration, from 1 after
+        a = opt.stats()["last_step"]
+        a_ref = (1.0 / g0_norm if it == 0 else 1.0) * 0.5 ** (ne_ref - 1)
+        assert abs(a - a_ref) <= 1e-12 * a_ref, (it, a, a_ref)
+        h_it = opt.history[-1]
+        assert h_it["step"] == a and h_it["evals"] == ne and h_it["loss"] == f
+        assert abs(h_it["relative_residual"] - (f / float(np.sum(W * I * I))) ** 0.5) <= 1e-12
     assert evals[0] == 4
+    assert opt.stats()["iterations"] == ref.n_iter == 12
+    assert opt.stats()["evaluations"] == ref.total_evals
     x = opt.get()[0].cpu().numpy().ravel()
     assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
 
@@ -148,6 +158,7 @@ def test_lbfgs_checkpoint_resume_continues_exactly(prec, tmp_path):
     xa = a.get()[0]
     b = tt.LBFGS.restore(h, np.load(path), Id)
     assert b.loss == loss_at_save
+    assert b.stats()["iterations"] == 6
     assert [b.step()[:2] for _ in range(5)] == cont
     assert torch.equal(b.get()[0], xa)
     other = tt.Handle(st, "f64" if prec == "f32" else "f32")
