@@ -137,7 +137,7 @@ def paper_shaped(torch, tt, synth, flush, steps: int = 20):
         z = torch.zeros_like(ct)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        opt = tt.LBFGS(h, z, It, None, m=10)
+        opt = tt.LBFGS(h, z, It, None, m=10, log=False)
         iters, evals = 0, 1
         for _ in range(20):
             _, ne, status = opt.step()
@@ -363,7 +363,7 @@ def make_inputs(st, torch, tt, synth):
 def reference_loss(h, I, W, torch, tt, ref_iters: int):
     """(L0, L*) of the plain FP32 solve: L* = loss after ref_iters L-BFGS iterations."""
     z = torch.zeros(h.volume_shape, dtype=torch.float32, device="cuda")
-    ref = tt.LBFGS(h, z, I, W, m=10)
+    ref = tt.LBFGS(h, z, I, W, m=10, log=False)
     L0 = ref.loss
     for _ in range(ref_iters):
         _, _, st = ref.step()
@@ -384,7 +384,7 @@ def time_to_loss(h, I, W, torch, tt, ref_iters: int, target: float = 1e-3, L0_Ls
     z = torch.zeros(h.volume_shape, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    opt = tt.LBFGS(h, z, I, W, m=10)
+    opt = tt.LBFGS(h, z, I, W, m=10, log=False)
     iters, evals = 0, 1
     while (opt.loss - Lstar) > target * (L0 - Lstar) and iters < ref_iters:
         _, ne, st = opt.step()
@@ -438,7 +438,7 @@ def noise_free_residual(h, c_true, torch, tt, target: float = 1e-3, max_iter: in
     z = torch.zeros(h.volume_shape, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    opt = tt.LBFGS(h, z, I, None, m=10)
+    opt = tt.LBFGS(h, z, I, None, m=10, log=False)
     it, ev = 0, 1
     while opt.loss ** 0.5 > target * nI and it < max_iter:
         _, ne, st_ = opt.step()

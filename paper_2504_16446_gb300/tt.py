@@ -338,7 +338,8 @@ class Handle:
 class LBFGS:
     """Device-resident L-BFGS on a Handle (tt_lbfgs_*)."""
 
-    def __init__(self, handle: Handle, c0: torch.Tensor, I: torch.Tensor, W: torch.Tensor | None = None, m: int = 10):
+    def __init__(self, handle: Handle, c0: torch.Tensor, I: torch.Tensor, W: torch.Tensor | None = None, m: int = 10,
+                 log: bool = True):
         self.h = handle
         handle._sync_stream()
         self._keep = (c0, I, W)
@@ -349,14 +350,16 @@ class LBFGS:
                "tt_lbfgs_create")
         self._st = st
         self.loss = self.get()[2]
-        self._start_log(I, W)
+        self._start_log(I, W, log)
 
-    def _start_log(self, I, W):
-        """Per-iteration log: loss, gradient evaluations, line-search step and
-        the relative data residual sqrt(L / sum W I^2)."""
-        Id = I.double()
-        self._data_norm2 = float(torch.sum(Id * Id if W is None else W.double() * Id * Id))
+    def _start_log(self, I, W, log):
+        """Per-iteration log (log=True): loss, gradient evaluations, line-search
+        step and the relative data residual sqrt(L / sum W I^2)."""
         self.history = []
+        self._data_norm2 = None
+        if log:
+            Id = I.double()
+            self._data_norm2 = float(torch.sum(Id * Id if W is None else W.double() * Id * Id))
 
     def stats(self) -> dict:
         """Accepted iterations, gradient evaluations (creation's included) and
@@ -376,7 +379,8 @@ class LBFGS:
         return buf
 
     @classmethod
-    def restore(cls, handle: "Handle", buf: np.ndarray, I: torch.Tensor, W: torch.Tensor | None = None) -> "LBFGS":
+    def restore(cls, handle: "Handle", buf: np.ndarray, I: torch.Tensor, W: torch.Tensor | None = None,
+                log: bool = True) -> "LBFGS":
         """A state from a checkpoint of save() (tt_lbfgs_restore); I and W as
         for the constructor."""
         handle._sync_stream()
@@ -391,7 +395,7 @@ class LBFGS:
         self._keep = (None, I, W)
         self._st = st
         self.loss = self.get()[2]
-        self._start_log(I, W)
+        self._start_log(I, W, log)
         return self
 
     def step(self):
@@ -403,9 +407,10 @@ class LBFGS:
         if st not in (TT_OK, TT_LINESEARCH_FAILED):
             _check(st, "tt_lbfgs_step")
         self.loss = loss.value
-        self.history.append({"loss": loss.value, "evals": ne.value, "step": self.stats()["last_step"],
-                             "relative_residual": (loss.value / self._data_norm2) ** 0.5
-                             if self._data_norm2 > 0 else float("nan"), "status": st})
+        if self._data_norm2 is not None:
+            self.history.append({"loss": loss.value, "evals": ne.value, "step": self.stats()["last_step"],
+                                 "relative_residual": (loss.value / self._data_norm2) ** 0.5
+                                 if self._data_norm2 > 0 else float("nan"), "status": st})
         return loss.value, ne.value, st
 
     def get(self):

@@ -50,7 +50,7 @@ def phantom_data(h: tt.Handle, st, n_ell: int, seed: int, mean_counts: float = 1
 def plain_solve(h: tt.Handle, I, iters: int, c0=None):
     """Plain FP32 L-BFGS (m = 10) from c0 (zero by default): (c, loss)."""
     z = torch.zeros(h.volume_shape, dtype=torch.float32, device="cuda") if c0 is None else c0
-    opt = tt.LBFGS(h, z, I, None, m=10)
+    opt = tt.LBFGS(h, z, I, None, m=10, log=False)
     for _ in range(iters):
         _, _, st = opt.step()
         if st != tt.TT_OK:
@@ -84,7 +84,7 @@ def iterations_to(h: tt.Handle, I, c0, L0: float, Lstar: float, target: float, m
     (L - L*)/(L0 - L*) <= target."""
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    opt = tt.LBFGS(h, c0, I, None, m=10)
+    opt = tt.LBFGS(h, c0, I, None, m=10, log=False)
     it, ev = 0, 1
     while (opt.loss - Lstar) > target * (L0 - Lstar) and it < max_iter:
         _, ne, st = opt.step()
