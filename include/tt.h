@@ -163,8 +163,13 @@ tt_status tt_adjoint_f64(tt_handle *h, const double *R_dev, double *g_dev);
  *   r = A c - I,  *loss_host = sum W r^2 (FP64 accumulation),
  *   g_dev = 2 A^T (W r).
  * W_dev may be NULL (all weights 1).  g_dev may be NULL (loss only).
- * loss_host is a HOST pointer; this call synchronises the handle's stream.
- * Returns TT_NONFINITE (with g and loss written) when the loss is not finite. */
+ * loss_host is a HOST pointer.  The call returns as soon as the loss is
+ * known: with g_dev the adjoint publishes it in a page-locked slot when it
+ * starts and may still be running on the handle's stream when the call
+ * returns (g_dev is stream-ordered like every device output; c, I and W have
+ * been consumed by then); without g_dev, or if no mapped slot could be
+ * allocated, the call synchronises the stream.  Returns TT_NONFINITE (the
+ * loss written, g following on the stream) when the loss is not finite. */
 tt_status tt_gradient_residual(tt_handle *h, const float *c_dev, const float *I_dev,
                                const float *W_dev, float *g_dev, double *loss_host);
 tt_status tt_gradient_residual_f64(tt_handle *h, const double *c_dev, const double *I_dev,

@@ -1,6 +1,7 @@
 // tt_api.cu -- C ABI of libtt: validation, geometry set-up (host, FP64),
 // buffer ownership and the orchestration of the kernels on the handle's stream.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -369,6 +370,7 @@ static void free_handle(tt_handle *h)
     for (cudaStream_t t : h->side)
         if (t) cudaStreamDestroy(t);
     if (h->loss_pinned) cudaFreeHost(h->loss_pinned);
+    if (h->loss_slot_host) cudaFreeHost(h->loss_slot_host);
     for (const auto &r : h->prof.pending) {
         cudaEventDestroy(r.begin);
         if (r.free_end) cudaEventDestroy(r.end);
@@ -447,6 +449,39 @@ tt_status tt_grad_enqueue(tt_handle *h, const T *c, const T *I, const T *W, T *g
 template tt_status tt_grad_enqueue<float>(tt_handle *, const float *, const float *, const float *, float *);
 template tt_status tt_grad_enqueue<double>(tt_handle *, const double *, const double *, const double *, double *);
 
+static tt_status check_finite_loss(double v)
+{
+    if (!std::isfinite(v)) {
+        set_error("loss is not finite (NaN/Inf in the inputs)");
+        return TT_NONFINITE;
+    }
+    return TT_OK;
+}
+
+tt_status tt_read_loss(tt_handle *h, double *loss_host);
+
+// Waits until the loss with sequence number seq is in the mapped slot, or
+// until the stream has drained (then the slot must hold it; if it does not,
+// the loss is copied as by tt_read_loss).  Errors of the stream are returned.
+static tt_status read_published_loss(tt_handle *h, unsigned long long seq, double *loss_host)
+{
+    const volatile LossSlot *slot = h->loss_slot_host;
+    for (;;) {
+        if (slot->seq == seq) break;
+        const cudaError_t q = cudaStreamQuery(h->stream);
+        if (q == cudaSuccess) {
+            if (slot->seq == seq) break;
+            return tt_read_loss(h, loss_host);
+        }
+        if (q != cudaErrorNotReady) return cuda_fail(q, "stream");
+        (void)cudaGetLastError();          // "not ready" is no error
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+    const double v = slot->value;
+    if (loss_host) *loss_host = v;
+    return check_finite_loss(v);
+}
+
 tt_status tt_read_loss(tt_handle *h, double *loss_host)
 {
     TT_CUDA(cudaMemcpyAsync(h->loss_pinned, h->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "loss copy");
@@ -464,9 +499,16 @@ template <typename T>
 static tt_status grad_impl(tt_handle *h, const T *c, const T *I, const T *W, T *g, double *loss_host)
 {
     if (!loss_host) return invalid("tt_gradient_residual: loss_host must not be NULL");
+    // With a gradient, the adjoint's first CTA publishes the loss in the
+    // mapped slot and the call returns once it is there; the rest of the
+    // adjoint stays in flight on the stream (g is stream-ordered like every
+    // device output).
+    const unsigned long long seq = (g && h->loss_slot_host) ? ++h->loss_seq : 0;
+    h->loss_publish = seq;
     tt_status st = tt_grad_enqueue<T>(h, c, I, W, g);
+    h->loss_publish = 0;
     if (st != TT_OK) return st;
-    return tt_read_loss(h, loss_host);
+    return seq ? read_published_loss(h, seq, loss_host) : tt_read_loss(h, loss_host);
 }
 
 // want = TT_F32 for the float entry points (handles of precision TT_F32,
@@ -563,6 +605,17 @@ tt_status tt_create(const tt_problem *P, tt_precision prec, void *stream, tt_han
     {
         cudaError_t e = cudaMallocHost((void **)&h->loss_pinned, sizeof(double) * 4);
         if (e != cudaSuccess) { free_handle(h); return cuda_fail(e, "tt_create: cudaMallocHost"); }
+        // the early-loss slot is optional: without a device mapping the loss
+        // is read after the whole evaluation, as by every other entry point
+        if (cudaHostAlloc((void **)&h->loss_slot_host, sizeof(LossSlot), cudaHostAllocMapped) == cudaSuccess) {
+            h->loss_slot_host->value = 0.0;
+            h->loss_slot_host->seq = 0;
+            if (cudaHostGetDevicePointer((void **)&h->loss_slot_dev, h->loss_slot_host, 0) != cudaSuccess) {
+                cudaFreeHost(h->loss_slot_host);
+                h->loss_slot_host = h->loss_slot_dev = nullptr;
+            }
+        }
+        (void)cudaGetLastError();
     }
     // basis matrix: stage [nodes][weights][frames 9S][seg0][seg1] and run the quadrature kernel
     std::vector<double> stage(2 * kQuadNodes + 9 * h->S + 2 * h->C);

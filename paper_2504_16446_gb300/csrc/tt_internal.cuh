@@ -86,6 +86,11 @@ struct AdjParams {
     AdjProj<T> p[kMax];
 };
 
+struct LossSlot {
+    double value;
+    unsigned long long seq;
+};
+
 struct Profile {
     struct Pending {
         cudaEvent_t begin, end;
@@ -128,6 +133,12 @@ struct tt_handle {
     double *red = nullptr;               // device, kDotBlocks partials of the regulariser reductions
     double *loss_dev = nullptr;          // device scalars: [0] loss, [1] regulariser value
     double *loss_pinned = nullptr;       // pinned host scalar
+    // Page-locked, device-mapped slot where the adjoint's first CTA publishes
+    // the loss of a gradient evaluation (value, then sequence number), so
+    // that tt_gradient_residual can return it while the adjoint still runs.
+    tt::LossSlot *loss_slot_host = nullptr, *loss_slot_dev = nullptr;
+    unsigned long long loss_seq = 0;     // last sequence number handed out
+    unsigned long long loss_publish = 0; // sequence number the next evaluation publishes (0: none)
     // host-buffer entry point staging (allocated on first use)
     void *hc = nullptr, *hI = nullptr, *hW = nullptr, *hg = nullptr;
     cudaStream_t copy_stream = nullptr;  // host-buffer path: data chunks copied while the forward runs

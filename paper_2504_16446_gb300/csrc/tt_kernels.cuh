@@ -573,14 +573,24 @@ template <typename T, typename S, int KP, int LG, int V>
 __global__ void __launch_bounds__(kThreads, (KP <= 16 ? 4 : 3))
 k_adjoint(const __grid_constant__ AdjParams<T> P, int ns, const S *__restrict__ G, int nj, int nk, int nx,
           int ny, int nz, int ty, int tz, T *__restrict__ gpad, int accumulate, T *__restrict__ gout, int K,
-          const double *__restrict__ loss_partials, long long n_partials, double *__restrict__ loss_out)
+          const double *__restrict__ loss_partials, long long n_partials, double *__restrict__ loss_out,
+          LossSlot *loss_slot, unsigned long long loss_seq)
 {
     // CTA 0 first sums the forward's loss partials (written by the previous
-    // launch on this stream, so visible here without fences).
+    // launch on this stream, so visible here without fences) and, given a
+    // host-mapped slot, publishes the value there: value, system-scope
+    // fence, then the sequence number the host waits for.
     if (loss_out && blockIdx.x == 0) {
         __shared__ double lred[32];
         const double v = sum_fixed_order(loss_partials, n_partials, lred);
-        if (threadIdx.x == 0) loss_out[0] = v;
+        if (threadIdx.x == 0) {
+            loss_out[0] = v;
+            if (loss_slot) {
+                *(volatile double *)&loss_slot->value = v;
+                __threadfence_system();
+                *(volatile unsigned long long *)&loss_slot->seq = loss_seq;
+            }
+        }
     }
     constexpr int CPL = KP / LG;
     // A warp's 32/LG lane groups take GZ consecutive z (times GX columns in
@@ -745,7 +755,8 @@ cudaError_t launch_adjoint_L(tt_handle *h, T *g, bool reduce_loss)
         k_adjoint<T, T, KP, LG, V><<<(unsigned)(tx * ty * tz), kThreads, 0, h->stream>>>(
             chunks[ci], ns, G + (size_t)s0 * h->nj * h->nk * KP, h->nj, h->nk, h->N[0], h->N[1], h->N[2], ty, tz,
             (T *)h->gpad, ci > 0 ? 1 : 0, last ? g : nullptr, h->K, h->partials, h->n_fwd_ctas,
-            (reduce_loss && ci == 0) ? h->loss_dev : nullptr);
+            (reduce_loss && ci == 0) ? h->loss_dev : nullptr,
+            (reduce_loss && ci == 0 && h->loss_publish) ? h->loss_slot_dev : nullptr, h->loss_publish);
         e = cudaGetLastError();
         prof_end(h, TT_KSLOT_ADJOINT, ev);
     }
