@@ -460,10 +460,16 @@ static tt_status check_finite_loss(double v)
 
 tt_status tt_read_loss(tt_handle *h, double *loss_host);
 
+unsigned long long loss_publish_begin(tt_handle *h)
+{
+    h->loss_publish = h->loss_slot_host ? ++h->loss_seq : 0;
+    return h->loss_publish;
+}
+
 // Waits until the loss with sequence number seq is in the mapped slot, or
 // until the stream has drained (then the slot must hold it; if it does not,
 // the loss is copied as by tt_read_loss).  Errors of the stream are returned.
-static tt_status read_published_loss(tt_handle *h, unsigned long long seq, double *loss_host)
+tt_status read_published_loss(tt_handle *h, unsigned long long seq, double *loss_host)
 {
     const volatile LossSlot *slot = h->loss_slot_host;
     for (;;) {
@@ -503,8 +509,7 @@ static tt_status grad_impl(tt_handle *h, const T *c, const T *I, const T *W, T *
     // mapped slot and the call returns once it is there; the rest of the
     // adjoint stays in flight on the stream (g is stream-ordered like every
     // device output).
-    const unsigned long long seq = (g && h->loss_slot_host) ? ++h->loss_seq : 0;
-    h->loss_publish = seq;
+    const unsigned long long seq = g ? loss_publish_begin(h) : 0;
     tt_status st = tt_grad_enqueue<T>(h, c, I, W, g);
     h->loss_publish = 0;
     if (st != TT_OK) return st;

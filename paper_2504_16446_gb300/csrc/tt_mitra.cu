@@ -22,6 +22,12 @@
 template <typename T>
 tt_status tt_grad_enqueue(tt_handle *h, const T *c, const T *I, const T *W, T *g);
 tt_status tt_read_loss(tt_handle *h, double *loss_host);
+// Early loss (tt_api.cu): loss_publish_begin makes the next adjoint launched
+// with reduce_loss publish the loss in the handle's mapped slot and returns
+// its sequence number (0 without a slot; the caller clears h->loss_publish
+// after enqueuing); read_published_loss waits for it.
+unsigned long long loss_publish_begin(tt_handle *h);
+tt_status read_published_loss(tt_handle *h, unsigned long long seq, double *loss_host);
 
 using namespace tt;
 
@@ -221,7 +227,11 @@ template <typename T>
 static tt_status mitra_step(tt_mitra *m, double *loss_host)
 {
     tt_handle *h = m->h;
+    // the loss (at y) is read as soon as the adjoint has published it; the
+    // update stays in flight behind it
+    const unsigned long long seq = loss_host ? loss_publish_begin(h) : 0;
     tt_status s = tt_grad_enqueue<T>(h, (const T *)m->y, (const T *)m->I, (const T *)m->R, (T *)m->g);
+    h->loss_publish = 0;
     if (s != TT_OK) return s;
     m->t += 1;
     const double t1 = m->t + 1;   // index of the next extrapolation
@@ -233,7 +243,8 @@ static tt_status mitra_step(tt_mitra *m, double *loss_host)
     cudaError_t e = cudaGetLastError();
     prof_end(h, TT_KSLOT_VECTOR, ev);
     if (e != cudaSuccess) return cuda_fail(e, "mitra update");
-    return loss_host ? tt_read_loss(h, loss_host) : TT_OK;
+    if (!loss_host) return TT_OK;
+    return seq ? read_published_loss(h, seq, loss_host) : tt_read_loss(h, loss_host);
 }
 
 extern "C" {
