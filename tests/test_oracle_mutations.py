@@ -1,7 +1,7 @@
 """The oracle's pins catch planted mistakes.  Each case copies the oracle,
 the pin tests and the input generators into a scratch directory, plants one
-plausible mistake in the copy of tt_oracle.c (a sign, an order, a dropped
-factor, a transposed index), and runs the pin suite there in a child
+plausible mistake in the copy of one oracle source (a sign, an order, a
+dropped factor, a transposed index), and runs the pin suite there in a child
 process: it must fail.  Nothing outside the scratch copy is touched."""
 import os
 import shutil
@@ -12,7 +12,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-# (name, original text, planted mistake) -- each original occurs exactly once
+# (name, original text, planted mistake) in tt_oracle.c -- each original occurs exactly once
 MUTATIONS = [
     ("rotation_sign", "R[3 * r + q] = (r == q ? 1.0 : 0.0) + s * K[3 * r + q] + (1.0 - c) * kk;",
      "R[3 * r + q] = (r == q ? 1.0 : 0.0) - s * K[3 * r + q] + (1.0 - c) * kk;"),
@@ -28,6 +28,11 @@ MUTATIONS = [
      "return ((size_t)xyz[2] * P->ny + xyz[1]) * P->nx + xyz[0];"),
     ("bilinear_weight", "double w = (du ? wu : 1.0 - wu) * (dv ? wv : 1.0 - wv);",
      "double w = (du ? 1.0 - wu : wu) * (dv ? wv : 1.0 - wv);"),
+    ("gradient_factor_two", "r[q] *= 2.0 * w;", "r[q] *= w;"),
+    ("weights_on_residual_not_square", "loss += w * r[q] * r[q];", "loss += r[q] * r[q];"),
+    ("segment_mean", "Bsc[i] += 0.5 * w[t] * y[i];", "Bsc[i] += half * w[t] * y[i];"),
+    ("legendre_recurrence", "plm = ((2.0 * ll - 1.0) * x * pm1m - (ll + m - 1.0) * pmm) / (ll - m);",
+     "plm = ((2.0 * ll - 1.0) * x * pm1m - (ll + m) * pmm) / (ll - m);"),
 ]
 
 
@@ -45,13 +50,23 @@ def _scratch_copy(dst):
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(tdst, "golden"))
 
 
-@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_pins_catch_a_planted_mistake(tmp_path, name, old, new):
-    src_path = os.path.join(ROOT, "oracle", "tt_oracle.c")
+# the same in the numpy parts of the oracle: (name, file, original, mistake)
+PY_MUTATIONS = [
+    ("lbfgs_initial_scaling", "lbfgs.py", "r = gamma * q", "r = q"),
+    ("huber_quadratic_branch", "regularizers.py", "t * t / (2.0 * delta)", "t * t / delta"),
+    ("nesterov_momentum", "sirt.py", "(t - 1.0) / (t + 2.0)", "t / (t + 2.0)"),
+    ("relu_dropped", "convnet.py", "y = rnd(np.maximum(y, 0.0))", "y = rnd(y)"),
+]
+CASES = [(n, "tt_oracle.c", o, w) for n, o, w in MUTATIONS] + PY_MUTATIONS
+
+
+@pytest.mark.parametrize("name,fname,old,new", CASES, ids=[m[0] for m in CASES])
+def test_pins_catch_a_planted_mistake(tmp_path, name, fname, old, new):
+    src_path = os.path.join(ROOT, "oracle", fname)
     src = open(src_path).read()
     assert src.count(old) == 1, name
     _scratch_copy(str(tmp_path))
-    with open(os.path.join(tmp_path, "oracle", "tt_oracle.c"), "w") as fh:
+    with open(os.path.join(tmp_path, "oracle", fname), "w") as fh:
         fh.write(src.replace(old, new))
     env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
