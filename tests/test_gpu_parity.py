@@ -119,6 +119,35 @@ def test_gradient_residual_fp64(kw):
     assert rel_l2(g.cpu().numpy(), g_ref) <= F64_TOL
 
 
+def test_early_loss_return_keeps_the_gradient_stream_ordered():
+    """tt_gradient_residual returns once the adjoint has published the loss,
+    with the adjoint still running.  Back-to-back evaluations of different
+    volumes, each gradient consumed on the stream right away (a clone and a
+    reduction) and no host synchronisation in between, give the same losses
+    and gradients as evaluations separated by full synchronisations."""
+    st = synth.workload("ell64")
+    h = tt.Handle(st, "f32")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    cs = [torch.randn(st.volume_shape, device="cuda", generator=gen) for _ in range(4)]
+    I = torch.rand(st.data_shape, device="cuda", generator=gen) * 64
+    torch.cuda.synchronize()
+    fast = []
+    for c in cs:
+        loss, g = h.gradient_residual(c, I)
+        fast.append((loss, g.clone(), g.double().sum()))
+    slow = []
+    for c in cs:
+        torch.cuda.synchronize()
+        loss, g = h.gradient_residual(c, I)
+        torch.cuda.synchronize()
+        slow.append((loss, g))
+    for (lf, gf, sf), (ls, gs) in zip(fast, slow):
+        assert lf == ls
+        torch.testing.assert_close(gf, gs, rtol=0, atol=0)
+        assert float(sf) == float(gs.double().sum())
+
+
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_loss_is_the_same_with_and_without_gradient(prec):
     """The loss partials are reduced by the adjoint's first CTA when a gradient
