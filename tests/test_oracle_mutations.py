@@ -53,6 +53,18 @@ def _scratch_copy(dst):
 # the same in the numpy parts of the oracle: (name, file, original, mistake)
 PY_MUTATIONS = [
     ("lbfgs_initial_scaling", "lbfgs.py", "r = gamma * q", "r = q"),
+    ("lbfgs_store_every_pair", "lbfgs.py", "if sy > 1e-10 * np.linalg.norm(s) * np.linalg.norm(y):",
+     "if sy > -1e300:"),
+    ("lbfgs_curvature_threshold", "lbfgs.py", "if sy > 1e-10 * np.linalg.norm(s)", "if sy > 1e-12 * np.linalg.norm(s)"),
+    ("lbfgs_no_descent_check", "lbfgs.py", "if gd >= 0.0:", "if gd > 1e300:"),
+    ("lbfgs_restart_keeps_memory", "lbfgs.py", "self.S.clear(); self.Y.clear(); self.rho.clear()", "pass"),
+    ("lbfgs_restart_unit_step", "lbfgs.py", "alpha = 1.0 / np.linalg.norm(self.g)", "alpha = 1.0"),
+    ("lbfgs_armijo_c1", "lbfgs.py", "c1: float = 1e-4", "c1: float = 1e-3"),
+    ("lbfgs_armijo_plain_decrease", "lbfgs.py", "if f_t <= self.f + self.c1 * alpha * gd:", "if f_t <= self.f:"),
+    ("lbfgs_halving", "lbfgs.py", "alpha *= 0.5", "alpha *= 0.25"),
+    ("lbfgs_max_evals", "lbfgs.py", "max_evals: int = 20", "max_evals: int = 21"),
+    ("lbfgs_failed_search_moves", "lbfgs.py", "        self.total_evals += self.max_evals\n",
+     "        self.total_evals += self.max_evals\n        self.x = x_t\n"),
     ("huber_quadratic_branch", "regularizers.py", "t * t / (2.0 * delta)", "t * t / delta"),
     ("nesterov_momentum", "sirt.py", "(t - 1.0) / (t + 2.0)", "t / (t + 2.0)"),
     ("relu_dropped", "convnet.py", "y = rnd(np.maximum(y, 0.0))", "y = rnd(y)"),
