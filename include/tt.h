@@ -118,6 +118,12 @@ const char *tt_last_error(void);
  * this call is the handle's device.  The handle owns all of its memory. */
 tt_status tt_create(const tt_problem *prob, tt_precision prec, void *stream, tt_handle **out);
 tt_status tt_destroy(tt_handle *h);
+/* Makes stream (cudaStream_t, NULL = legacy default stream) the handle's
+ * stream for the calls that follow.  When it differs from the current one,
+ * the new stream is ordered behind everything already enqueued on the old
+ * stream (an event, no host synchronisation), so work still in flight there
+ * (e.g. the adjoint behind an early-returned loss) is done with the handle's
+ * buffers before the new stream reuses them. */
 tt_status tt_set_stream(tt_handle *h, void *stream);
 /* Shape query: any out-pointer may be NULL. */
 tt_status tt_get_sizes(const tt_handle *h, int *K, int *K_padded, long long *n_vox, long long *n_data);
@@ -140,12 +146,15 @@ tt_status tt_basis_matrix(tt_handle *h, double *B_dev);
  * ell_max <= 12 as for tt_create); larger problems return TT_INVALID_ARG.
  * prob is validated like tt_create's; B_dev (device, [n_proj][n_seg][K]
  * doubles, 16-byte aligned) receives the result, enqueued on stream
- * (cudaStream_t, NULL = legacy default stream).  The first call on each
- * device looks up the scratch array's device address (the device must be
- * current); make that first call before any stream capture.  All calls
- * share the one scratch array, which keeps the last call's contents; every
- * call overwrites what it reads, so nothing needs clearing, but calls whose
- * work overlaps on the GPU (other streams, other host threads) race on it. */
+ * (cudaStream_t, NULL = legacy default stream).  The inputs are staged
+ * through a per-thread pageable host buffer: the staging copy waits for the
+ * work already enqueued on stream before it starts, and its bytes are staged
+ * by the time the call returns.  The first call on each device looks up the
+ * scratch array's device address (the device must be current); make that
+ * first call before any stream capture.  All calls share the one scratch
+ * array, which keeps the last call's contents; every call overwrites what it
+ * reads, so nothing needs clearing, but calls whose work overlaps on the GPU
+ * (other streams, other host threads) race on it. */
 tt_status tt_basis_matrix_noalloc(const tt_problem *prob, double *B_dev, void *stream);
 
 /* Forward model, Eq. (forward_model): I = A c.
@@ -279,8 +288,11 @@ tt_status tt_sirt_weights_f64(tt_handle *h, const double *W_dev, double *R_dev, 
 tt_status tt_mitra_create(tt_handle *h, const void *c0_dev, const void *I_dev, const void *W_dev,
                           double eta, double momentum, tt_mitra **out);
 /* One iteration: one gradient-residual evaluation at y_t and one update
- * kernel.  loss_host (may be NULL) receives L_R(y_t) and synchronises the
- * stream; with NULL the call only enqueues work (no host synchronisation). */
+ * kernel.  loss_host (may be NULL) receives L_R(y_t): the call returns as
+ * soon as the adjoint has published that loss, with the rest of the adjoint
+ * and the update kernel still in flight (x and y are stream-ordered outputs,
+ * like every device result).  With NULL the call only enqueues work (no host
+ * synchronisation). */
 tt_status tt_mitra_step(tt_mitra *m, double *loss_host);
 /* Copies the iterate x (c_dev, [nx][ny][nz][K]), the data weights R
  * (R_dev) and the preconditioner D (D_dev); any may be NULL.  *iterations

@@ -31,6 +31,25 @@ tt_status cuda_fail(cudaError_t e, const char *what)
         if (_e != cudaSuccess) return ::tt::cuda_fail(_e, what); \
     } while (0)
 
+int current_sm_count()
+{
+    static std::atomic<int> cache[256];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+        (void)cudaGetLastError();
+        return 1;
+    }
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n < 1) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+            (void)cudaGetLastError();
+            return 1;
+        }
+        cache[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
 static tt_status invalid(const std::string &msg)
 {
     set_error(msg);
@@ -159,22 +178,31 @@ static void apply_transpose(const double R[9], const double *v, double *out)
 
 struct Frames { double p[3], j[3], k[3], q0[3], q90[3]; };
 
-static Frames projection_frames(const tt_handle *h, int s)
+// Sample-frame vectors R_s^T v of one projection, R_s = R_beta(beta) R_alpha(alpha).
+static Frames frames_of(const tt_frame &fr, double alpha, double beta)
 {
     double ax[3], bx[3];
-    const double na = norm3(h->frame.inner_axis), nb = norm3(h->frame.outer_axis);
-    for (int t = 0; t < 3; ++t) { ax[t] = h->frame.inner_axis[t] / na; bx[t] = h->frame.outer_axis[t] / nb; }
+    const double na = norm3(fr.inner_axis), nb = norm3(fr.outer_axis);
+    for (int t = 0; t < 3; ++t) { ax[t] = fr.inner_axis[t] / na; bx[t] = fr.outer_axis[t] / nb; }
     double Ra[9], Rb[9], R[9];
-    axis_angle(ax, h->inner[s], Ra);
-    axis_angle(bx, h->outer[s], Rb);
+    axis_angle(ax, alpha, Ra);
+    axis_angle(bx, beta, Rb);
     matmul3(Rb, Ra, R);                      // R_s = R_beta(beta) R_alpha(alpha)
     Frames f;
-    apply_transpose(R, h->frame.p, f.p);
-    apply_transpose(R, h->frame.j, f.j);
-    apply_transpose(R, h->frame.k, f.k);
-    apply_transpose(R, h->frame.q0, f.q0);
-    apply_transpose(R, h->frame.q90, f.q90);
+    apply_transpose(R, fr.p, f.p);
+    apply_transpose(R, fr.j, f.j);
+    apply_transpose(R, fr.k, f.k);
+    apply_transpose(R, fr.q0, f.q0);
+    apply_transpose(R, fr.q90, f.q90);
     return f;
+}
+
+static Frames projection_frames(const tt_handle *h, int s) { return frames_of(h->frame, h->inner[s], h->outer[s]); }
+
+void basis_frame(const tt_frame &fr, double alpha, double beta, double out[9])
+{
+    const Frames f = frames_of(fr, alpha, beta);
+    for (int t = 0; t < 3; ++t) { out[t] = f.p[t]; out[3 + t] = f.q0[t]; out[6 + t] = f.q90[t]; }
 }
 
 static ProjGeom make_geom(const tt_handle *h, int s)
@@ -369,6 +397,7 @@ static void free_handle(tt_handle *h)
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     for (cudaStream_t t : h->side)
         if (t) cudaStreamDestroy(t);
+    if (h->stream_switch) cudaEventDestroy(h->stream_switch);
     if (h->loss_pinned) cudaFreeHost(h->loss_pinned);
     if (h->loss_slot_host) cudaFreeHost(h->loss_slot_host);
     for (const auto &r : h->prof.pending) {
@@ -562,7 +591,17 @@ tt_status tt_create(const tt_problem *P, tt_precision prec, void *stream, tt_han
     if (!h) return TT_OUT_OF_MEMORY;
     h->prec = prec;
     cudaGetDevice(&h->dev);
+    if (cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->dev) != cudaSuccess || h->n_sm < 1) {
+        delete h;
+        set_error("tt_create: cannot query the multiprocessor count of the current device");
+        return TT_CUDA_ERROR;
+    }
     h->stream = (cudaStream_t)stream;
+    if (cudaEventCreateWithFlags(&h->stream_switch, cudaEventDisableTiming) != cudaSuccess) {
+        delete h;
+        set_error("tt_create: cudaEventCreate failed");
+        return TT_CUDA_ERROR;
+    }
     h->N[0] = P->nx; h->N[1] = P->ny; h->N[2] = P->nz;
     h->nj = P->nj; h->nk = P->nk; h->S = P->n_proj; h->L = P->ell_max; h->C = P->n_seg;
     h->K = num_coeffs(h->L);
@@ -606,7 +645,7 @@ tt_status tt_create(const tt_problem *P, tt_precision prec, void *stream, tt_han
     h->n_partials = h->n_fwd_ctas;
     ALLOC(h->partials, sizeof(double) * h->n_partials);
     ALLOC(h->loss_dev, sizeof(double) * 4);
-    ALLOC(h->red, sizeof(double) * kDotBlocks);
+    ALLOC(h->red, sizeof(double) * dot_blocks(h));
     {
         cudaError_t e = cudaMallocHost((void **)&h->loss_pinned, sizeof(double) * 4);
         if (e != cudaSuccess) { free_handle(h); return cuda_fail(e, "tt_create: cudaMallocHost"); }
@@ -625,11 +664,7 @@ tt_status tt_create(const tt_problem *P, tt_precision prec, void *stream, tt_han
     // basis matrix: stage [nodes][weights][frames 9S][seg0][seg1] and run the quadrature kernel
     std::vector<double> stage(2 * kQuadNodes + 9 * h->S + 2 * h->C);
     gauss_legendre(kQuadNodes, stage.data(), stage.data() + kQuadNodes);
-    for (int s = 0; s < h->S; ++s) {
-        const Frames f = projection_frames(h, s);
-        double *F = stage.data() + 2 * kQuadNodes + 9 * s;
-        for (int t = 0; t < 3; ++t) { F[t] = f.p[t]; F[3 + t] = f.q0[t]; F[6 + t] = f.q90[t]; }
-    }
+    for (int s = 0; s < h->S; ++s) basis_frame(h->frame, h->inner[s], h->outer[s], stage.data() + 2 * kQuadNodes + 9 * s);
     std::memcpy(stage.data() + 2 * kQuadNodes + 9 * h->S, h->seg0.data(), sizeof(double) * h->C);
     std::memcpy(stage.data() + 2 * kQuadNodes + 9 * h->S + h->C, h->seg1.data(), sizeof(double) * h->C);
     double *dstage = nullptr;
@@ -661,7 +696,14 @@ tt_status tt_destroy(tt_handle *h)
 tt_status tt_set_stream(tt_handle *h, void *stream)
 {
     if (!h) return invalid("null handle");
-    h->stream = (cudaStream_t)stream;
+    const cudaStream_t next = (cudaStream_t)stream;
+    if (next == h->stream) return TT_OK;
+    // Order the new stream behind everything already enqueued on the old
+    // one (no host synchronisation): the handle's scratch (G, partials,
+    // the packed volume, the loss slot) may still be in use there.
+    TT_CUDA(cudaEventRecord(h->stream_switch, h->stream), "tt_set_stream: event record");
+    TT_CUDA(cudaStreamWaitEvent(next, h->stream_switch, 0), "tt_set_stream: stream wait");
+    h->stream = next;
     return TT_OK;
 }
 

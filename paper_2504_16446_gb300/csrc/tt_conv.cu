@@ -427,22 +427,13 @@ __global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float
     }
 }
 
+static int sm_count() { return current_sm_count(); }
+
 static unsigned grid_n(long long n)
 {
+    const long long cap = 16LL * sm_count();
     long long b = (n + 255) / 256;
-    return (unsigned)(b < 1 ? 1 : (b > 152LL * 16 ? 152LL * 16 : b));
-}
-
-static int sm_count()
-{
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n < 1) n = 1;
-    }
-    return n;
+    return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
 // Launches the forward convolution (tcgen05 kernel) for a (CIN, COUT) pair:
@@ -509,7 +500,6 @@ __global__ void k_reduce(const double *__restrict__ partials, long long n, doubl
 
 constexpr int kNetLayers = 4;
 constexpr int kHidden = 32;
-constexpr int kLossBlocks = 608;
 
 static int layer_cin(int l) { return l == 0 ? 16 : kHidden; }
 static int layer_cout(int l) { return l == kNetLayers - 1 ? 16 : kHidden; }
@@ -522,6 +512,7 @@ using namespace tt;
 struct tt_wsnet {
     int kin = 0, kout = 0;
     cudaStream_t stream = nullptr;
+    int loss_blocks = 0;                 // CTAs of the loss reduction (four per SM)
     float *w[kNetLayers] = {}, *gw[kNetLayers] = {}, *m[kNetLayers] = {}, *v[kNetLayers] = {};
     __nv_bfloat16 *wk[kNetLayers] = {}, *wt[kNetLayers] = {};
     long long step = 0;
@@ -610,10 +601,10 @@ static tt_status net_gradient(tt_wsnet *n, int nx, int ny, int nz, const float *
     tt_status st = net_forward(n, nx, ny, nz, x, 1.0 / in_scale);
     if (st != TT_OK) return st;
     const double count = (double)nvox * n->kout;
-    k_sq_error<<<kLossBlocks, 256, 0, n->stream>>>(n->out, tgt, (float)(1.0 / out_scale), n->kout, nvox, 1.0 / count,
+    k_sq_error<<<n->loss_blocks, 256, 0, n->stream>>>(n->out, tgt, (float)(1.0 / out_scale), n->kout, nvox, 1.0 / count,
                                                      n->dout, n->partials);
     TT_NET_CUDA(cudaGetLastError(), "wsnet loss");
-    k_reduce<<<1, 256, 0, n->stream>>>(n->partials, kLossBlocks, n->loss_dev, nullptr, 1.0 / count);
+    k_reduce<<<1, 256, 0, n->stream>>>(n->partials, n->loss_blocks, n->loss_dev, nullptr, 1.0 / count);
     TT_NET_CUDA(cudaGetLastError(), "wsnet loss reduce");
     for (int l = 0; l < kNetLayers; ++l)
         TT_NET_CUDA(cudaMemsetAsync(n->gw[l], 0, sizeof(float) * wsize(l), n->stream), "wsnet memset");
@@ -671,7 +662,8 @@ tt_status tt_wsnet_create(int k_in, int k_out, const float *w_host, void *stream
         if (e == cudaSuccess) e = cudaMemsetAsync(n->m[l], 0, b, n->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(n->v[l], 0, b, n->stream);
     }
-    if (e == cudaSuccess) e = cudaMalloc(&n->partials, sizeof(double) * kLossBlocks);
+    n->loss_blocks = 4 * sm_count();
+    if (e == cudaSuccess) e = cudaMalloc(&n->partials, sizeof(double) * n->loss_blocks);
     if (e == cudaSuccess) e = cudaMalloc(&n->loss_dev, sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&n->loss_pinned, sizeof(double));
     if (e != cudaSuccess) { free_net(n); return cuda_fail(e, "tt_wsnet_create"); }

@@ -113,7 +113,13 @@ struct Profile {
 struct tt_handle {
     tt_precision prec;
     int dev;
+    int n_sm = 0;                        // streaming multiprocessors of dev (grid sizing)
     cudaStream_t stream;
+    // Recorded on the old stream when tt_set_stream switches streams; the
+    // new stream waits on it, so work still in flight on the old stream
+    // (an adjoint behind an early-returned loss) finishes with the handle's
+    // buffers before the new stream reuses them.
+    cudaEvent_t stream_switch = nullptr;
     int N[3];
     int nj, nk, S, L, K, KP, LG, C, CP;
     double a, b, two_theta;
@@ -130,7 +136,7 @@ struct tt_handle {
     double *partials = nullptr;          // device, per-CTA loss partials
     long long n_partials = 0;            // allocated entries
     long long n_fwd_ctas = 0;            // entries the forward kernel writes
-    double *red = nullptr;               // device, kDotBlocks partials of the regulariser reductions
+    double *red = nullptr;               // device, dot_blocks(h) partials of the regulariser reductions
     double *loss_dev = nullptr;          // device scalars: [0] loss, [1] regulariser value
     double *loss_pinned = nullptr;       // pinned host scalar
     // Page-locked, device-mapped slot where the adjoint's first CTA publishes
@@ -235,6 +241,9 @@ tt_status cuda_fail(cudaError_t e, const char *what);
 // Problem validation and Gauss-Legendre rule shared by the entry points.
 tt_status validate(const tt_problem *P);
 void gauss_legendre(int n, double *x, double *w);
+// The rows k_basis reads for one projection: R_s^T p, R_s^T q0, R_s^T q90
+// (R_s = R_beta(outer angle) R_alpha(inner angle), FP64), 9 doubles.
+void basis_frame(const tt_frame &fr, double inner_angle, double outer_angle, double out[9]);
 
 template <typename T>
 const std::vector<AdjParams<T>> &adj_params(const tt_handle *h);
@@ -294,6 +303,11 @@ template <typename T>
 cudaError_t vec_axpby(tt_handle *h, T *y, const T *x, long long n, double ha, const double *da, double hb);
 template <typename T>
 cudaError_t vec_sub(tt_handle *h, T *out, const T *x, const T *y, long long n);
-constexpr int kDotBlocks = 608;   // 4 x 152 SMs
+// Streaming-multiprocessor count of the current device (queried once per
+// device ordinal and cached); grids of the grid-stride kernels are capped at
+// multiples of it.
+int current_sm_count();
+// CTAs of the dot-product and regulariser reductions: four per SM.
+inline int dot_blocks(const tt_handle *h) { return 4 * h->n_sm; }
 
 }  // namespace tt

@@ -39,17 +39,13 @@ using namespace tt;
 namespace {
 
 constexpr int kMaxM = 64;
-#ifndef TT_PAIR_BLOCKS
-#define TT_PAIR_BLOCKS 608
-#endif
-constexpr int kPairBlocks = TT_PAIR_BLOCKS;   // CTAs of the pair / cross dot kernels (4 per SM)
 
 // Blocks of the per-element kernels (four elements per thread): a multiple of
 // the SM count, capped.
 unsigned elem_blocks(long long n)
 {
     long long b = (n / 4 + 255) / 256;
-    return (unsigned)std::max(1LL, std::min(b, 152LL * 16));
+    return (unsigned)std::max(1LL, std::min(b, 16LL * current_sm_count()));
 }
 
 // Four consecutive elements as one 16-byte access (two for double).  Every
@@ -315,6 +311,7 @@ struct tt_lbfgs {
     double *part = nullptr;       // device partials
     double *dots = nullptr;       // device row sums
     double *pinned = nullptr;     // host copy of dots
+    int pair_blocks = 0;          // CTAs of the pair / cross dot kernels (four per SM)
     int nb = 2 * kMaxM + 1;
     double &G(int i, int j) { return gram[(size_t)i * nb + j]; }
     int iS(int slot) const { return slot; }
@@ -423,16 +420,16 @@ static tt_status enqueue_pair_dots(tt_lbfgs *st, const std::vector<int> &used)
     const int nu = (int)used.size();
     cudaEvent_t ev;
     prof_begin(h, TT_KSLOT_VECTOR, &ev);
-    k_pair<T><<<kPairBlocks, 256, 0, h->stream>>>((const T *)st->x, (const T *)st->xt, (const T *)st->g,
+    k_pair<T><<<st->pair_blocks, 256, 0, h->stream>>>((const T *)st->x, (const T *)st->xt, (const T *)st->g,
                                                 (const T *)st->gt, (T *)st->ss, (T *)st->ys, st->n, st->part);
     if (nu > 0) {
         Slots<T> sl;
         for (int u = 0; u < nu; ++u) { sl.S[u] = (const T *)st->S[used[u]]; sl.Y[u] = (const T *)st->Y[used[u]]; }
-        k_cross<T><<<dim3(kPairBlocks, (nu + 1) / 2), 256, 0, h->stream>>>(
-            sl, nu, (const T *)st->ss, (const T *)st->ys, (const T *)st->gt, st->n, st->part + 6 * kPairBlocks);
+        k_cross<T><<<dim3(st->pair_blocks, (nu + 1) / 2), 256, 0, h->stream>>>(
+            sl, nu, (const T *)st->ss, (const T *)st->ys, (const T *)st->gt, st->n, st->part + 6 * st->pair_blocks);
     }
     const int rows = 6 + 6 * nu;
-    k_rows<<<rows, 256, 0, h->stream>>>(st->part, kPairBlocks, st->dots);
+    k_rows<<<rows, 256, 0, h->stream>>>(st->part, st->pair_blocks, st->dots);
     cudaError_t e = cudaGetLastError();
     prof_end(h, TT_KSLOT_VECTOR, ev);
     TT_CUDA(e, "lbfgs pair dots");
@@ -586,7 +583,8 @@ static tt_status alloc_state(tt_handle *h, int m, const void *I, const void *W, 
         st->Y[i] = base; base += pitch;
     }
     const size_t rows = 6 + 6 * (size_t)m;
-    e = cudaMalloc(&st->part, sizeof(double) * std::max<size_t>(rows * kPairBlocks, kDotBlocks));
+    st->pair_blocks = 4 * h->n_sm;
+    e = cudaMalloc(&st->part, sizeof(double) * std::max<size_t>(rows * st->pair_blocks, dot_blocks(h)));
     if (e == cudaSuccess) e = cudaMalloc(&st->dots, sizeof(double) * rows);
     if (e == cudaSuccess) e = cudaMallocHost(&st->pinned, sizeof(double) * rows);
     if (e != cudaSuccess) { free_state(st); return cuda_fail(e, "L-BFGS state"); }

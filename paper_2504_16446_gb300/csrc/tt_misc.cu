@@ -60,7 +60,8 @@ __global__ void k_unpack(const T *__restrict__ gpad, T *__restrict__ g, long lon
 static unsigned grid_for(long long n, int per_block = 256)
 {
     long long b = (n + per_block - 1) / per_block;
-    if (b > 152LL * 32) b = 152LL * 32;
+    const long long cap = 32LL * current_sm_count();
+    if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (unsigned)b;
 }
@@ -174,11 +175,11 @@ cudaError_t vec_dot(tt_handle *h, const T *x, const T *y, long long n, double *p
 {
     cudaEvent_t ev;
     prof_begin(h, TT_KSLOT_VECTOR, &ev);
-    k_dot_partial<T><<<kDotBlocks, 256, 0, h->stream>>>(x, y, n, partials);
+    k_dot_partial<T><<<dot_blocks(h), 256, 0, h->stream>>>(x, y, n, partials);
     cudaError_t e = cudaGetLastError();
     prof_end(h, TT_KSLOT_VECTOR, ev);
     if (e != cudaSuccess) return e;
-    return launch_reduce(h, partials, kDotBlocks, out, add, mul);
+    return launch_reduce(h, partials, dot_blocks(h), out, add, mul);
 }
 
 template <typename T>

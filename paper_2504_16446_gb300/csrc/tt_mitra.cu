@@ -44,7 +44,8 @@ constexpr double kY00 = 0.28209479177387814347;   // 1 / (2 sqrt(pi))
 unsigned blocks_for(long long n)
 {
     long long b = (n + 255) / 256;
-    if (b > 152LL * 32) b = 152LL * 32;
+    const long long cap = 32LL * current_sm_count();
+    if (b > cap) b = cap;
     return (unsigned)(b < 1 ? 1 : b);
 }
 

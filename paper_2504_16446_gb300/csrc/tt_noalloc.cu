@@ -29,16 +29,6 @@ static double *g_scratch_addr[256];          // device address of g_basis_scratc
 
 static thread_local double t_host_stage[kNoAllocDoubles];
 
-static void rodrigues(const double *n_in, double t, double R[9])
-{
-    const double nn = std::sqrt(n_in[0] * n_in[0] + n_in[1] * n_in[1] + n_in[2] * n_in[2]);
-    const double x = n_in[0] / nn, y = n_in[1] / nn, z = n_in[2] / nn;
-    const double c = std::cos(t), s = std::sin(t), C1 = 1.0 - c;
-    R[0] = c + x * x * C1;     R[1] = x * y * C1 - z * s; R[2] = x * z * C1 + y * s;
-    R[3] = y * x * C1 + z * s; R[4] = c + y * y * C1;     R[5] = y * z * C1 - x * s;
-    R[6] = z * x * C1 - y * s; R[7] = z * y * C1 + x * s; R[8] = c + z * z * C1;
-}
-
 }  // namespace tt
 
 extern "C" tt_status tt_basis_matrix_noalloc(const tt_problem *prob, double *B_dev, void *stream)
@@ -84,23 +74,16 @@ extern "C" tt_status tt_basis_matrix_noalloc(const tt_problem *prob, double *B_d
     const int S = prob->n_proj, C = prob->n_seg, L = prob->ell_max, K = (L + 1) * (L + 2) / 2;
     double *hs = t_host_stage;
     gauss_legendre(kQuadNodes, hs, hs + kQuadNodes);
-    for (int s = 0; s < S; ++s) {
-        double Ra[9], Rb[9], R[9];
-        rodrigues(prob->frame.inner_axis, prob->inner_angle[s], Ra);
-        rodrigues(prob->frame.outer_axis, prob->outer_angle[s], Rb);
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) R[3 * r + c] = Rb[3 * r] * Ra[c] + Rb[3 * r + 1] * Ra[3 + c] + Rb[3 * r + 2] * Ra[6 + c];
-        const double *vecs[3] = {prob->frame.p, prob->frame.q0, prob->frame.q90};
-        double *F = hs + 2 * kQuadNodes + 9 * s;
-        for (int t = 0; t < 3; ++t)
-            for (int c = 0; c < 3; ++c)       // R_s^T v
-                F[3 * t + c] = R[c] * vecs[t][0] + R[3 + c] * vecs[t][1] + R[6 + c] * vecs[t][2];
-    }
+    // the same frames as tt_create stages (one shared helper)
+    for (int s = 0; s < S; ++s) basis_frame(prob->frame, prob->inner_angle[s], prob->outer_angle[s], hs + 2 * kQuadNodes + 9 * s);
     double *seg0 = hs + 2 * kQuadNodes + 9 * S, *seg1 = seg0 + C;
     for (int c = 0; c < C; ++c) { seg0[c] = prob->seg_start[c]; seg1[c] = prob->seg_end[c]; }
     const size_t n = (size_t)(2 * kQuadNodes + 9 * S + 2 * C);
 
     cudaStream_t strm = (cudaStream_t)stream;
+    // A copy from pageable host memory: the runtime waits for the work
+    // already on strm, then stages the bytes before this call returns, so
+    // the thread's staging buffer may be reused by its next call.
     e = cudaMemcpyAsync(scratch, hs, n * sizeof(double), cudaMemcpyHostToDevice, strm);
     if (e != cudaSuccess) return cuda_fail(e, "tt_basis_matrix_noalloc: staging copy");
     const double th = 0.5 * prob->two_theta;

@@ -84,10 +84,10 @@ __global__ void k_tv_huber(const T *__restrict__ c, int nx, int ny, int nz, int 
     if (threadIdx.x == 0) partials[blockIdx.x] = v;
 }
 
-static unsigned reg_grid(long long n)
+static unsigned reg_grid(const tt_handle *h, long long n)
 {
     long long b = (n + 255) / 256;
-    return (unsigned)(b < 1 ? 1 : (b > kDotBlocks ? kDotBlocks : b));
+    return (unsigned)(b < 1 ? 1 : (b > dot_blocks(h) ? dot_blocks(h) : b));
 }
 
 template <typename T>
@@ -112,7 +112,7 @@ template <typename T>
 static tt_status l2_impl(tt_handle *h, const T *c, T *grad, double *value_host)
 {
     const long long n = h->nvox() * h->K;
-    const unsigned blocks = reg_grid(n);
+    const unsigned blocks = reg_grid(h, n);
     cudaEvent_t ev;
     prof_begin(h, TT_KSLOT_VECTOR, &ev);
     k_l2<T><<<blocks, 256, 0, h->stream>>>(c, n, grad, h->red);
@@ -124,7 +124,7 @@ template <typename T>
 static tt_status tv_impl(tt_handle *h, const T *c, double delta, T *grad, double *value_host)
 {
     const long long n = h->nvox() * h->K;
-    const unsigned blocks = reg_grid(n);
+    const unsigned blocks = reg_grid(h, n);
     cudaEvent_t ev;
     prof_begin(h, TT_KSLOT_VECTOR, &ev);
     k_tv_huber<T><<<blocks, 256, 0, h->stream>>>(c, h->N[0], h->N[1], h->N[2], h->K, (T)delta, grad, h->red);

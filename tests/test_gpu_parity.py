@@ -148,6 +148,35 @@ def test_early_loss_return_keeps_the_gradient_stream_ordered():
         assert float(sf) == float(gs.double().sum())
 
 
+def test_switching_streams_orders_the_handle_behind_work_in_flight():
+    """Evaluations alternate between two torch streams with no host
+    synchronisation: each returns once its loss is published, its adjoint
+    still running on the old stream when the next call switches the handle to
+    the other stream and overwrites the handle's buffers.  tt_set_stream
+    orders the new stream behind the old one, so losses and gradients equal
+    those of fully synchronised evaluations bit for bit."""
+    st = synth.workload("ell64")
+    h = tt.Handle(st, "f32")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(9)
+    cs = [torch.randn(st.volume_shape, device="cuda", generator=gen) for _ in range(6)]
+    I = torch.rand(st.data_shape, device="cuda", generator=gen) * 64
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    torch.cuda.synchronize()
+    fast = []
+    for i, c in enumerate(cs):
+        with torch.cuda.stream(streams[i % 2]):
+            loss, g = h.gradient_residual(c, I)
+            fast.append((loss, g.clone()))
+    torch.cuda.synchronize()
+    for (lf, gf), c in zip(fast, cs):
+        torch.cuda.synchronize()
+        ls, gs = h.gradient_residual(c, I)
+        torch.cuda.synchronize()
+        assert lf == ls
+        torch.testing.assert_close(gf, gs, rtol=0, atol=0)
+
+
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_loss_is_the_same_with_and_without_gradient(prec):
     """The loss partials are reduced by the adjoint's first CTA when a gradient

@@ -68,3 +68,21 @@ def test_noalloc_rejects_more_projections_than_its_scratch_holds():
     status = lib.tt_basis_matrix_noalloc(ctypes.byref(P), ctypes.c_void_p(16), None)
     assert status == tt.TT_INVALID_ARG
     assert b"2048" in lib.tt_last_error()
+
+
+@pytest.mark.gpu
+def test_noalloc_basis_matrix_at_full_scratch_capacity():
+    """2048 projections, 64 segments and l_max 12 fill the fixed scratch to
+    its last element (a 4^3 volume and 4 x 4 pixels keep the rest small); the
+    result equals the handle entry point's on two calls in a row."""
+    build.build()
+    lib = tt.load()
+    st = synth.small_setup(n=(4, 4, 4), nj=4, nk=4, ell_max=12, n_proj=2048, n_seg=64, seed=11, two_theta=0.2)
+    h = tt.Handle(st, "f32")
+    ref = h.basis_matrix()
+    torch.cuda.synchronize()
+    h.close()
+    for _ in range(2):
+        out = torch.full_like(ref, float("nan"))
+        assert _noalloc(lib, st, out) == tt.TT_OK, lib.tt_last_error()
+        np.testing.assert_allclose(out.cpu().numpy(), ref.cpu().numpy(), atol=1e-13, rtol=0)
