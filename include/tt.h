@@ -341,6 +341,12 @@ tt_status tt_wsnet_get_weights(tt_wsnet *net, float *w_host);
  * cin, cout in {16, 32}. */
 tt_status tt_conv3d_bf16(int nx, int ny, int nz, int cin, int cout, const void *x_dev, const void *w_dev, int relu,
                          float *y_dev, void *stream);
+/* The network's hidden-layer form of the same convolution: y_dev bfloat16
+ * [nvox][cout] (raw 16-bit words), the FP32 accumulation with ReLU (relu !=
+ * 0) rounded once to bfloat16.  Compiled for (cin, cout) = (16, 32) and
+ * (32, 32), and without ReLU also (32, 16); other pairs: TT_UNSUPPORTED. */
+tt_status tt_conv3d_bf16_act(int nx, int ny, int nz, int cin, int cout, const void *x_dev, const void *w_dev,
+                             int relu, void *y_dev, void *stream);
 tt_status tt_conv3d_wgrad_bf16(int nx, int ny, int nz, int cin, int cout, const void *x_dev, const void *dy_dev,
                                float *dw_dev, void *stream);
 

@@ -205,21 +205,35 @@ void basis_frame(const tt_frame &fr, double alpha, double beta, double out[9])
     for (int t = 0; t < 3; ++t) { out[t] = f.p[t]; out[3 + t] = f.q0[t]; out[6 + t] = f.q90[t]; }
 }
 
+// Main axis of the Joseph march: the largest |p_s| component, ties to the
+// smallest axis.
+static int main_axis(const double *d)
+{
+    const double mx = std::fmax(std::fabs(d[0]), std::fmax(std::fabs(d[1]), std::fabs(d[2])));
+    int m = 0;
+    while (std::fabs(d[m]) < (1.0 - 1e-12) * mx) ++m;
+    return m;
+}
+
 static ProjGeom make_geom(const tt_handle *h, int s)
 {
     const Frames f = projection_frames(h, s);
     const double *d = f.p;
-    const double mx = std::fmax(std::fabs(d[0]), std::fmax(std::fabs(d[1]), std::fabs(d[2])));
-    int m = 0;
-    while (std::fabs(d[m]) < (1.0 - 1e-12) * mx) ++m;   // ties -> smallest axis
-    const int u = (m == 0) ? 1 : 0;
-    const int v = (m == 2) ? 1 : 2;
-    const int stride[3] = {(h->N[1] + 4) * (h->N[2] + 4), h->N[2] + 4, 1};   // padded volume
+    const int m = main_axis(d);
+    // The transverse axis v is the innermost axis of the copy the projection
+    // reads: z for m = x, y (cpad), x for m = z (the x-innermost copy).
+    const int copy = (m == 2) ? 1 : 0;
+    const int u = (m == 0) ? 1 : (m == 1 ? 0 : 1);
+    const int v = (m == 2) ? 0 : 2;
+    const int stride_z[3] = {(h->N[1] + 4) * (h->N[2] + 4), h->N[2] + 4, 1};
+    const int stride_x[3] = {1, h->N[0] + 4, (h->N[1] + 4) * (h->N[0] + 4)};
+    const int *stride = copy ? stride_x : stride_z;
     const double ba = h->b / h->a;
     const double cj = 0.5 * (h->nj - 1) + h->joff[s], ck = 0.5 * (h->nk - 1) + h->koff[s];
     const double hm = 0.5 * (h->N[m] - 1), hu = 0.5 * (h->N[u] - 1), hv = 0.5 * (h->N[v] - 1);
     ProjGeom g;
     g.m = m; g.u = u; g.v = v;
+    g.copy = copy;
     g.Nm = h->N[m]; g.Nu = h->N[u]; g.Nv = h->N[v];
     g.sm = stride[m]; g.su = stride[u]; g.sv = stride[v];
     g.up = d[u] / d[m];
@@ -410,7 +424,7 @@ static void free_handle(tt_handle *h)
 
 static long long forward_ctas(const tt_handle *h)
 {
-    const int rays = kThreads / h->LG, TK = 8, TJ = rays / TK;
+    const int TK = fwd_tk(h->LG), TJ = fwd_tj(h->LG);
     return (long long)((h->nk + TK - 1) / TK) * ((h->nj + TJ - 1) / TJ) * h->S;
 }
 
@@ -619,7 +633,10 @@ tt_status tt_create(const tt_problem *P, tt_precision prec, void *stream, tt_han
     h->seg0.assign(P->seg_start, P->seg_start + h->C);
     h->seg1.assign(P->seg_end, P->seg_end + h->C);
     h->geo_host.resize(h->S);
-    for (int s = 0; s < h->S; ++s) h->geo_host[s] = make_geom(h, s);
+    for (int s = 0; s < h->S; ++s) {
+        h->geo_host[s] = make_geom(h, s);
+        h->xcopy = h->xcopy || h->geo_host[s].copy == 1;
+    }
     if (prec != TT_F64) build_adj_params<float>(h, h->adj_f32);
     else build_adj_params<double>(h, h->adj_f64);
 
@@ -634,9 +651,12 @@ tt_status tt_create(const tt_problem *P, tt_precision prec, void *stream, tt_han
     ALLOC(h->Bp, es * h->S * h->CP * h->KP);
     {
         const long long padded = (long long)(h->N[0] + 4) * (h->N[1] + 4) * (h->N[2] + 4);
-        ALLOC(h->cpad, h->ssize() * padded * h->KP);
+        const long long copies = h->xcopy ? 2 : 1;
+        h->pad_vox = padded;
+        ALLOC(h->cpad, h->ssize() * copies * padded * h->KP);
         h->cpad_origin = 2LL * (h->N[1] + 4) * (h->N[2] + 4) + 2LL * (h->N[2] + 4) + 2;
-        cudaError_t ez = cudaMemsetAsync(h->cpad, 0, h->ssize() * padded * h->KP, h->stream);   // border stays zero
+        h->cpadx_origin = 2LL * (h->N[1] + 4) * (h->N[0] + 4) + 2LL * (h->N[0] + 4) + 2;
+        cudaError_t ez = cudaMemsetAsync(h->cpad, 0, h->ssize() * copies * padded * h->KP, h->stream);   // border stays zero
         if (ez != cudaSuccess) { free_handle(h); return cuda_fail(ez, "tt_create: memset"); }
     }
     ALLOC(h->gpad, es * h->nvox() * h->KP);

@@ -91,31 +91,54 @@ struct TcConvSmem {
 
 // Stages input plane gx (zeros outside the volume) into a plane buffer:
 // chunk (kc, yh, zl) = voxel (gx, y0-1+yh, z0-1+zl), channels 8 kc .. 8 kc+7.
+// Two phases, so that the global loads can be in flight while the thread
+// waits for MMAs and writes a tile out: plane_load into registers, then
+// plane_store into the buffer.
+template <int CIN>
+struct PlaneRegs {
+    static constexpr int KC = CIN / 8, kChunks = KC * 6 * 32, kPer = (kChunks + kTcThreads - 1) / kTcThreads;
+    uint4 val[kPer];
+};
+
+template <int CIN>
+__device__ __forceinline__ void plane_load(PlaneRegs<CIN> &r, const __nv_bfloat16 *__restrict__ in, int gx, int y0,
+                                           int z0, int nx, int ny, int nz, int tid)
+{
+    using P = PlaneRegs<CIN>;
+#pragma unroll
+    for (int j = 0; j < P::kPer; ++j) {
+        const int e = tid + j * kTcThreads;
+        r.val[j] = make_uint4(0, 0, 0, 0);
+        if (e < P::kChunks) {
+            const int zl = e % 32, kc = (e / 32) % P::KC, yh = e / (32 * P::KC);
+            const int gy = y0 - 1 + yh, gz = z0 - 1 + zl;
+            if ((unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz)
+                r.val[j] = __ldg(reinterpret_cast<const uint4 *>(in + (((size_t)gx * ny + gy) * nz + gz) * CIN) + kc);
+        }
+    }
+}
+
+template <int CIN>
+__device__ __forceinline__ void plane_store(uint8_t *buf, const PlaneRegs<CIN> &r, int tid)
+{
+    using P = PlaneRegs<CIN>;
+#pragma unroll
+    for (int j = 0; j < P::kPer; ++j) {
+        const int e = tid + j * kTcThreads;
+        if (e < P::kChunks) {
+            const int zl = e % 32, kc = (e / 32) % P::KC, yh = e / (32 * P::KC);
+            *reinterpret_cast<uint4 *>(buf + (kc * 6 + yh) * 512 + zl * 16) = r.val[j];
+        }
+    }
+}
+
 template <int CIN>
 __device__ __forceinline__ void stage_plane(uint8_t *buf, const __nv_bfloat16 *__restrict__ in, int gx, int y0,
                                             int z0, int nx, int ny, int nz, int tid)
 {
-    constexpr int KC = CIN / 8, kChunks = KC * 6 * 32, kPer = (kChunks + kTcThreads - 1) / kTcThreads;
-    uint4 val[kPer];
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-        const int e = tid + j * kTcThreads;
-        val[j] = make_uint4(0, 0, 0, 0);
-        if (e < kChunks) {
-            const int zl = e % 32, kc = (e / 32) % KC, yh = e / (32 * KC);
-            const int gy = y0 - 1 + yh, gz = z0 - 1 + zl;
-            if ((unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz)
-                val[j] = __ldg(reinterpret_cast<const uint4 *>(in + (((size_t)gx * ny + gy) * nz + gz) * CIN) + kc);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-        const int e = tid + j * kTcThreads;
-        if (e < kChunks) {
-            const int zl = e % 32, kc = (e / 32) % KC, yh = e / (32 * KC);
-            *reinterpret_cast<uint4 *>(buf + (kc * 6 + yh) * 512 + zl * 16) = val[j];
-        }
-    }
+    PlaneRegs<CIN> r;
+    plane_load<CIN>(r, in, gx, y0, z0, nx, ny, nz, tid);
+    plane_store<CIN>(buf, r, tid);
 }
 
 // Tile epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. (input rows
@@ -228,6 +251,12 @@ k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__res
                 }
                 umma::mma_commit(mbar + (i & 1));
             }
+            // plane x+2 (for tile x+1): its loads go out now, overlapping the
+            // running MMAs and tile x-1's write-out; the stores wait until the
+            // MMAs of tile x-1, the last reader of that ring buffer, are done
+            PlaneRegs<CIN> next;
+            const bool stage = x + 2 <= xb;
+            if (stage) plane_load<CIN>(next, in, x + 2, y0, z0, nx, ny, nz, tid);
             if (i > 0) {
                 const int p = (i - 1) & 1;
                 const bool ok = umma::mbar_wait(mbar + p, issued[p] & 1u, kTcWaitTries);
@@ -236,10 +265,9 @@ k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__res
                 tile_epilogue<COUT, RELU, OUT_F32>(tmem, (uint32_t)(NB * p), ok, out, x - 1, y0, z0, ny, nz, warp,
                                                    lane);
             }
-            // plane x+2 (for tile x+1) into the buffer tile x-1 read; its MMAs are done
-            if (x + 2 <= xb) {
+            if (stage) {
                 umma::fence_async_smem();
-                stage_plane<CIN>(smem + ((x + 2) & 3) * L::plane, in, x + 2, y0, z0, nx, ny, nz, tid);
+                plane_store<CIN>(smem + ((x + 2) & 3) * L::plane, next, tid);
             }
         }
         umma::fence_before_sync();
@@ -791,6 +819,26 @@ tt_status tt_conv3d_bf16(int nx, int ny, int nz, int cin, int cout, const void *
     TT_NET_CUDA(conv3d_forward((const __nv_bfloat16 *)x, (const __nv_bfloat16 *)w, y, nx, ny, nz, cin, cout, false,
                                true, (cudaStream_t)stream),
                 "tt_conv3d_bf16");
+    return TT_OK;
+}
+
+// The network's hidden-layer form: y = conv(x, w), ReLU optional, y
+// [nvox][cout] bfloat16 (raw 16-bit), the output rounded once from the FP32
+// accumulation.
+tt_status tt_conv3d_bf16_act(int nx, int ny, int nz, int cin, int cout, const void *x, const void *w, int relu,
+                             void *y, void *stream)
+{
+    if (!x || !w || !y || bad_dims(nx, ny, nz) || (cin != 16 && cin != 32) || (cout != 16 && cout != 32)) {
+        set_error("tt_conv3d_bf16_act: bad arguments");
+        return TT_INVALID_ARG;
+    }
+    if ((cin == 16 && cout == 16) || (relu && cout != 32)) {
+        set_error("tt_conv3d_bf16_act: compiled for (cin, cout) = (16, 32), (32, 32) and, without ReLU, (32, 16)");
+        return TT_UNSUPPORTED;
+    }
+    TT_NET_CUDA(conv3d_forward((const __nv_bfloat16 *)x, (const __nv_bfloat16 *)w, y, nx, ny, nz, cin, cout,
+                               relu != 0, false, (cudaStream_t)stream),
+                "tt_conv3d_bf16_act");
     return TT_OK;
 }
 

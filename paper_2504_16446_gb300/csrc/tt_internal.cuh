@@ -17,7 +17,15 @@ namespace tt {
 constexpr int kMaxEll = 12;
 constexpr int kMaxSeg = 64;
 constexpr int kQuadNodes = 32;      // Gauss-Legendre nodes per detector segment
-constexpr int kThreads = 256;       // threads per CTA of the projector kernels
+constexpr int kThreads = 256;       // threads per CTA of the adjoint and the other projector kernels
+// Threads of a forward CTA and the ray tile it marches: fwd_tk(LG) rays along
+// k (fastest) times fwd_tj(LG) along j, lane_group(K) lanes per ray (8 x 8
+// rays at K = 15; 512- and 1024-thread tiles of 16 x 8 and 16 x 16 rays were
+// measured 5% and 20% slower at 64^3).
+constexpr int kFwdThreads = 256;
+__host__ __device__ constexpr int fwd_rays(int LG) { return kFwdThreads / LG; }
+__host__ __device__ constexpr int fwd_tk(int LG) { return fwd_rays(LG) >= 256 ? 16 : 8; }
+__host__ __device__ constexpr int fwd_tj(int LG) { return fwd_rays(LG) / fwd_tk(LG); }
 
 // Lane-group width (lanes that share one ray or one voxel, each holding
 // KP/LG channels) and padded channel count for a band limit.
@@ -57,7 +65,8 @@ struct ProjGeom {
     double hj, hk;            // half extents in j and k of the rays around a voxel (|du|, |dv| < 1)
     int m, u, v;              // main and transverse axes (0=x, 1=y, 2=z)
     int Nm, Nu, Nv;
-    int sm, su, sv;           // strides of the axes in the padded volume cpad
+    int sm, su, sv;           // strides of the axes in the padded volume copy the projection reads
+    int copy;                 // 0: cpad (z innermost), 1: the x-innermost copy; sv == 1 in both
 };
 
 // Per-projection constants of the adjoint gather in the element type.  The
@@ -129,8 +138,16 @@ struct tt_handle {
     tt::ProjGeom *geo = nullptr;        // device [S]
     double *B64 = nullptr;               // device [S][C][K] FP64
     void *Bp = nullptr;                  // device [S][CP][KP], element type, zero padded
-    void *cpad = nullptr;                // device [nx+4][ny+4][nz+4][KP], two-voxel zero border
+    // Padded coefficient volume, two-voxel zero border, channel innermost:
+    // [nx+4][ny+4][nz+4][KP] (z innermost) and, when some projection's main
+    // axis is z, a second copy [nz+4][ny+4][nx+4][KP] (x innermost) right
+    // after it, so that every projection has a transverse axis of stride one
+    // and a bilinear tap pair along it is one contiguous 2*KP-element piece.
+    void *cpad = nullptr;
     long long cpad_origin = 0;           // voxel offset of (0,0,0) in cpad
+    bool xcopy = false;                  // the x-innermost copy exists
+    long long pad_vox = 0;               // voxels of one padded copy
+    long long cpadx_origin = 0;          // voxel offset of (0,0,0) in the x-innermost copy (from its start)
     void *gpad = nullptr;                // device [nvox][KP]
     void *G = nullptr;                   // device [S][nj][nk][KP]
     double *partials = nullptr;          // device, per-CTA loss partials

@@ -124,6 +124,74 @@ __device__ __forceinline__ void fma_row_s(T (&acc)[CPL], T w, const S *__restric
     }
 }
 
+// ----------------------------------------------------- wide row-piece loads
+// NB bytes from p (aligned to ALIGN bytes) as 32-bit words, in pieces of 32
+// bytes (the 256-bit global load of sm_100+) where size and alignment allow,
+// else 16 or 8.  A quarter-warp whose lanes read one contiguous 128-byte run
+// moves it as one L1 wavefront; lanes of four-lane groups reading separate
+// 64-byte rows take about 1.45x the wavefronts for the same bytes.  SAFE:
+// every address the caller can form is in bounds, even for an iteration the
+// compiler executes speculatively, so the 256-bit load may be scheduled
+// freely (not volatile) and loads of several planes overlap.
+template <int NB, int ALIGN, bool SAFE = false>
+__device__ __forceinline__ void ldg_words(const void *p, unsigned (&w)[NB / 4])
+{
+    constexpr int PIECE = (ALIGN >= 32 && NB % 32 == 0) ? 32 : ((ALIGN >= 16 && NB % 16 == 0) ? 16 : 8);
+    static_assert(NB % PIECE == 0 && ALIGN >= 8, "row pieces are whole 8-byte words");
+    const char *b = reinterpret_cast<const char *>(p);
+#pragma unroll
+    for (int t = 0; t < NB / PIECE; ++t) {
+        if constexpr (PIECE == 32) {
+            unsigned *o = w + 8 * t;
+            if constexpr (SAFE)
+                asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                    : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]), "=r"(o[7])
+                    : "l"(b + 32 * t));
+            else
+                asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                             : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]),
+                               "=r"(o[7])
+                             : "l"(b + 32 * t));
+        } else if constexpr (PIECE == 16) {
+            const uint4 u = __ldg(reinterpret_cast<const uint4 *>(b + 16 * t));
+            w[4 * t] = u.x; w[4 * t + 1] = u.y; w[4 * t + 2] = u.z; w[4 * t + 3] = u.w;
+        } else {
+            const uint2 u = __ldg(reinterpret_cast<const uint2 *>(b + 8 * t));
+            w[2 * t] = u.x; w[2 * t + 1] = u.y;
+        }
+    }
+}
+
+// Element e of S held in the words w, converted to T.
+template <typename T, typename S, int NW>
+__device__ __forceinline__ T word_elem(const unsigned (&w)[NW], int e)
+{
+    if constexpr (std::is_same<S, float>::value) {
+        return __uint_as_float(w[e]);
+    } else if constexpr (std::is_same<S, double>::value) {
+        return __hiloint2double((int)w[2 * e + 1], (int)w[2 * e]);
+    } else {
+        const float2 f = unpack2(w[e / 2], (S *)nullptr);
+        return (e & 1) ? f.y : f.x;
+    }
+}
+
+// acc[i] += wt * x[OFS + i] for i < N, x the NE elements of S held in w;
+// paired FP32 FMAs for float.
+template <typename T, typename S, int N, int OFS, int NW>
+__device__ __forceinline__ void fma_words(T (&acc)[N], T wt, const unsigned (&w)[NW])
+{
+    if constexpr (std::is_same<T, float>::value) {
+        static_assert(N % 2 == 0 && OFS % 2 == 0, "paired FMAs");
+#pragma unroll
+        for (int i = 0; i < N; i += 2)
+            fma2(acc[i], acc[i + 1], wt, word_elem<T, S>(w, OFS + i), word_elem<T, S>(w, OFS + i + 1));
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) acc[i] = fma(wt, word_elem<T, S>(w, OFS + i), acc[i]);
+    }
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -187,12 +255,14 @@ __device__ __forceinline__ void clip_planes(T w0, T dw, int N, T &lo, T &hi)
 // SH contraction of a marched ray and, in GRAD mode, the residual, its
 // weighted square and the back-contraction (Eq. forward_model, Eq. residual).
 // The contraction runs four segments at a time: partial dot products over the
-// lane's CPL channels, a butterfly across the LG lanes of the channel group,
-// then each lane back-contracts into its own channels.  Lanes with
+// lane's CPL channels (chunk `chunk` of the row), a butterfly across the LG
+// lanes of the channel group, then each lane back-contracts into its own
+// channels.  Lanes with
 // writer == false (duplicate halves) compute but do not store.  Returns the
 // ray's sum of W r^2 on every lane.
 template <typename T, typename S, int CPL, int KP, int LG, bool GRAD>
-__device__ __forceinline__ T forward_epilogue(const T (&acc)[CPL], int q, bool valid, bool writer, long long pix,
+__device__ __forceinline__ T forward_epilogue(const T (&acc)[CPL], int q, int chunk, bool valid, bool writer,
+                                              long long pix,
                                               const T *__restrict__ Bs, int C, int CP, T *__restrict__ Iout,
                                               const T *__restrict__ Id, const T *__restrict__ Wd,
                                               T *__restrict__ G)
@@ -201,12 +271,13 @@ __device__ __forceinline__ T forward_epilogue(const T (&acc)[CPL], int q, bool v
 #pragma unroll
     for (int i = 0; i < CPL; ++i) gacc[i] = T(0);
     T lossr = T(0);
+    const int boff = chunk * CPL;
     const bool vec4 = (C % 4) == 0;
     for (int c0 = 0; c0 < CP; c0 += 4) {
         T ih[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            const T *brow = Bs + (c0 + t) * KP + q * CPL;
+            const T *brow = Bs + (c0 + t) * KP + boff;
             T sacc = T(0);
 #pragma unroll
             for (int i = 0; i < CPL; ++i) sacc = fma(brow[i], acc[i], sacc);
@@ -259,14 +330,14 @@ __device__ __forceinline__ T forward_epilogue(const T (&acc)[CPL], int q, bool v
                 const T rr = live ? ih[t] - dI[t] : T(0);
                 const T wr = live ? dW[t] * rr : T(0);
                 lossr = fma(wr, rr, lossr);
-                const T *brow = Bs + (c0 + t) * KP + q * CPL;
+                const T *brow = Bs + (c0 + t) * KP + boff;
 #pragma unroll
                 for (int i = 0; i < CPL; ++i) gacc[i] = fma(brow[i], wr, gacc[i]);
             }
         }
     }
     if constexpr (GRAD) {
-        if (valid && writer) store_row<T, CPL>(G + pix * KP + q * CPL, gacc, T(2));
+        if (valid && writer) store_row<T, CPL>(G + pix * KP + chunk * CPL, gacc, T(2));
     }
     return lossr;
 }
@@ -282,20 +353,19 @@ __device__ __forceinline__ T forward_epilogue(const T (&acc)[CPL], int q, bool v
 // the lane's channels, a butterfly across the lane group, then each lane
 // back-contracts into its own channels.
 template <typename T, typename S, int KP, int LG, bool GRAD>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kFwdThreads)
 k_forward(const ProjGeom *__restrict__ geo, const S *__restrict__ cpad /* interior origin */,
-          const T *__restrict__ Bp,
+          const S *__restrict__ cpadx /* interior origin of the x-innermost copy, or NULL */, const T *__restrict__ Bp,
           int nj, int nk, int C, int CP, int tiles_k, int slab_order, int s_base,
           T *__restrict__ Iout, const T *__restrict__ Id, const T *__restrict__ Wd,
           T *__restrict__ G, double *__restrict__ partials)
 {
     constexpr int CPL = KP / LG;
-    constexpr int RAYS = kThreads / LG;
-    constexpr int TK = 8;
-    constexpr int TJ = RAYS / TK;
+    constexpr int TK = fwd_tk(LG);
+    constexpr int TJ = fwd_tj(LG);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *Bs = reinterpret_cast<T *>(smem_raw);   // [CP][KP]
-    __shared__ double red[kThreads / 32];
+    __shared__ double red[kFwdThreads / 32];
 
     // CTA order.  slab_order == 0: all tiles of one projection, projection by
     // projection (gridDim = (tiles_k * tiles_j, S)).  slab_order == 1: k tile
@@ -313,58 +383,101 @@ k_forward(const ProjGeom *__restrict__ geo, const S *__restrict__ cpad /* interi
     const bool valid = (j < nj) && (k < nk);
 
     const T *Bsrc = Bp + (size_t)s * CP * KP;
-    for (int t = threadIdx.x; t < CP * KP; t += kThreads) Bs[t] = Bsrc[t];
+    for (int t = threadIdx.x; t < CP * KP; t += kFwdThreads) Bs[t] = Bsrc[t];
 
     const ProjGeom &P = geo[s];
     // Ray base in FP64 (one rounding to T), per-plane stepping in T.
     const double urd = P.u0 + (double)j * P.uj + (double)k * P.uk;
     const double vrd = P.v0 + (double)j * P.vj + (double)k * P.vk;
     const T ur = (T)urd, vr = (T)vrd, up = (T)P.up, vp = (T)P.vp;
-    const int Nu = P.Nu, Nv = P.Nv, sm = P.sm, su = P.su, sv = P.sv;
+    const int Nu = P.Nu, Nv = P.Nv, sm = P.sm, su = P.su;
     T lo = T(0), hi = T(P.Nm - 1);
     clip_planes<T>(ur, up, Nu, lo, hi);
     clip_planes<T>(vr, vp, Nv, lo, hi);
     int plo = valid ? max(0, (int)floor(lo)) : 1;
     int phi = valid ? min(P.Nm - 1, (int)ceil(hi)) : 0;
 
-    T acc[CPL];
+    // The march reads bilinear taps in pairs along v, the innermost axis of
+    // the volume copy this projection reads (sv == 1): rows (iu, iv) and
+    // (iu, iv + 1) are one contiguous piece of 2 KP elements, and likewise
+    // at iu + 1.  Lane q of the group reads part q of each pair, NP = 2 KP /
+    // LG elements: for LG >= 2 that is row iv + h, h = q / (LG / 2), channels
+    // [cofs, cofs + NP); a lone lane (LG == 1) reads both rows.  Lanes h = 0
+    // and h = 1 sum their halves once the ray is marched.
+    constexpr int NP = 2 * KP / LG;
+    constexpr int ACH = LG == 1 ? KP : NP;          // channels a lane accumulates
+    constexpr int ROWB = KP * (int)sizeof(S);
+    constexpr int PIECEB = NP * (int)sizeof(S);
+    constexpr int ALIGN = LG == 1 ? (ROWB & -ROWB) : ((ROWB | PIECEB) & -(ROWB | PIECEB));
+    constexpr int NW = PIECEB / 4;
+    const int h = LG == 1 ? 0 : q / (LG / 2);
+    const int cofs = LG == 1 ? 0 : (q % (LG / 2)) * NP;
+    T acc[ACH];
 #pragma unroll
-    for (int i = 0; i < CPL; ++i) acc[i] = T(0);
+    for (int i = 0; i < ACH; ++i) acc[i] = T(0);
     // cpad is the interior origin of a volume with a two-voxel zero border:
-    // every tap index in [-2, N+1] is a valid address, so the four loads need
-    // no bounds tests (indices are clamped to [-2, N] first, which only ever
+    // every tap index in [-2, N+1] is a valid address, so the loads need no
+    // bounds tests (indices are clamped to [-2, N] first, which only ever
     // moves a tap pair that lies wholly in the border).
-    const S *cq = cpad + q * CPL;
-    const long long sub = (long long)su * KP, svb = (long long)sv * KP;
+    const S *cq = (P.copy ? cpadx : cpad) + q * NP;
+    const long long sub = (long long)su * KP;
     // Reduced-precision storage (S = bf16 / f16) is read and converted per
     // tap; the ray sum stays a plain FP32 accumulation: over N planes its
     // rounding (~N 2^-24) is far below the 2^-9 / 2^-12 rounding of the
     // stored values (compensated sums were measured to change the projection
     // by < 1e-9 relative, at 10% of the kernel's time).
-    // Rows wider than 16 channels march two planes per iteration (more loads
-    // in flight at the same occupancy: 10% faster at K = 45, 2% at K = 28);
-    // at K_p <= 16 the unrolled loop was measured 2.5% slower.
-#pragma unroll(KP > 16 ? 2 : 1)
+    // Loads in flight per lane: 32-channel rows march two planes per
+    // iteration and 2-byte rows of up to 16 channels four (measured at 64^3:
+    // bfloat16 0.313 -> 0.277 ms); FP32 rows of 16 channels hold 16 words
+    // per plane already, and unrolling them was measured slower.
+    constexpr int kUnroll = KP == 32 ? 2 : ((sizeof(S) == 2 && KP <= 16) ? 4 : 1);
+#pragma unroll kUnroll
     for (int p = plo; p <= phi; ++p) {
         const T u = fma((T)p, up, ur), v = fma((T)p, vp, vr);
         const T fu = floor(u), fv = floor(v);
         const int iu = min(max((int)fu, -2), Nu), iv = min(max((int)fv, -2), Nv);
         const T wu = u - fu, wv = v - fv;
-        const S *t00 = cq + ((long long)p * sm + (long long)iu * su + (long long)iv * sv) * KP;
-        const T a0 = T(1) - wu, b0 = T(1) - wv;
-        fma_row_s<T, S, CPL>(acc, a0 * b0, t00);
-        fma_row_s<T, S, CPL>(acc, wu * b0, t00 + sub);
-        fma_row_s<T, S, CPL>(acc, a0 * wv, t00 + svb);
-        fma_row_s<T, S, CPL>(acc, wu * wv, t00 + sub + svb);
+        const S *t0 = cq + ((long long)p * sm + (long long)iu * su + iv) * KP;
+        unsigned x0[NW], x1[NW];
+        // any p in [plo - 1, phi + 1] and the clamped iu, iv address the padded
+        // volume (two-voxel border), so the loads may run speculatively
+        ldg_words<PIECEB, ALIGN, true>(t0, x0);
+        ldg_words<PIECEB, ALIGN, true>(t0 + sub, x1);
+        if constexpr (LG >= 2) {
+            const T wvh = h ? wv : T(1) - wv;
+            fma_words<T, S, ACH, 0>(acc, (T(1) - wu) * wvh, x0);
+            fma_words<T, S, ACH, 0>(acc, wu * wvh, x1);
+        } else {
+            const T a0 = T(1) - wu, b0 = T(1) - wv;
+            fma_words<T, S, ACH, 0>(acc, a0 * b0, x0);
+            fma_words<T, S, ACH, KP>(acc, a0 * wv, x0);
+            fma_words<T, S, ACH, 0>(acc, wu * b0, x1);
+            fma_words<T, S, ACH, KP>(acc, wu * wv, x1);
+        }
+    }
+    // Both rows' sums in every lane of a pair, then lane q keeps channel
+    // chunk `chunk` (CPL channels) for the epilogue.
+    T accq[CPL];
+    int chunk = 0;
+    if constexpr (LG >= 2) {
+#pragma unroll
+        for (int i = 0; i < ACH; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], LG / 2);
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) accq[i] = h ? acc[CPL + i] : acc[i];
+        chunk = cofs / CPL + h;
+    } else {
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) accq[i] = acc[i];
     }
     const T step = (T)P.step;
 #pragma unroll
-    for (int i = 0; i < CPL; ++i) acc[i] *= step;
+    for (int i = 0; i < CPL; ++i) accq[i] *= step;
 
     __syncthreads();   // Bs staged
 
     const long long pix = ((long long)s * nj + j) * nk + k;
-    const T lossr = forward_epilogue<T, S, CPL, KP, LG, GRAD>(acc, q, valid, true, pix, Bs, C, CP, Iout, Id, Wd, G);
+    const T lossr = forward_epilogue<T, S, CPL, KP, LG, GRAD>(accq, q, chunk, valid, true, pix, Bs, C, CP, Iout, Id,
+                                                              Wd, G);
     if constexpr (GRAD) {
         double tot;
         if constexpr (std::is_same<T, float>::value)
@@ -691,7 +804,7 @@ cudaError_t launch_forward_L(tt_handle *h, T *Iout, const T *I, const T *W, bool
     if (s1 < 0) s1 = h->S;
     const int ns = s1 - s0;
     constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K);
-    constexpr int RAYS = kThreads / LG, TK = 8, TJ = RAYS / TK;
+    constexpr int TK = fwd_tk(LG), TJ = fwd_tj(LG);
     const int tiles_k = (h->nk + TK - 1) / TK, tiles_j = (h->nj + TJ - 1) / TJ;
     // slab order once the padded volume would take more than half of L2
     const long long vol_bytes = (long long)(h->N[0] + 4) * (h->N[1] + 4) * (h->N[2] + 4) * KP * sizeof(S);
@@ -700,17 +813,18 @@ cudaError_t launch_forward_L(tt_handle *h, T *Iout, const T *I, const T *W, bool
     const size_t smem = (size_t)h->CP * KP * sizeof(T);
     const T *Bp = (const T *)h->Bp;
     const S *cpad = (const S *)h->cpad + h->cpad_origin * KP;
+    const S *cpadx = h->xcopy ? (const S *)h->cpad + (h->pad_vox + h->cpadx_origin) * KP : nullptr;
     cudaEvent_t ev;
     prof_begin(h, TT_KSLOT_FORWARD, &ev);
     if (grad) {
         auto kern = k_forward<T, S, KP, LG, true>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<grid, kThreads, smem, h->stream>>>(h->geo, cpad, Bp, h->nj, h->nk, h->C, h->CP, tiles_k, slab, s0,
+        kern<<<grid, kFwdThreads, smem, h->stream>>>(h->geo, cpad, cpadx, Bp, h->nj, h->nk, h->C, h->CP, tiles_k, slab, s0,
                                                  nullptr, I, W, (T *)h->G, h->partials);
     } else {
         auto kern = k_forward<T, S, KP, LG, false>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<grid, kThreads, smem, h->stream>>>(h->geo, cpad, Bp, h->nj, h->nk, h->C, h->CP, tiles_k, slab, s0,
+        kern<<<grid, kFwdThreads, smem, h->stream>>>(h->geo, cpad, cpadx, Bp, h->nj, h->nk, h->C, h->CP, tiles_k, slab, s0,
                                                  Iout, nullptr, nullptr, nullptr, nullptr);
     }
     cudaError_t e = cudaGetLastError();

@@ -8,7 +8,8 @@ namespace tt {
 // ------------------------------------------------------------- layout
 
 // Interior of the padded volume: cpad[x+2][y+2][z+2][i] = c[x][y][z][i] for
-// i < K, 0 for K <= i < KP (the two-voxel border is zeroed once at creation).
+// i < K, 0 for K <= i < KP (the two-voxel border is zeroed once at creation);
+// with cpadx, also the x-innermost copy cpadx[z+2][y+2][x+2][i].
 // One thread per 4-channel chunk of a voxel: consecutive threads read
 // consecutive chunks of c and write consecutive 16-byte (8-byte for 2-byte
 // storage) pieces of cpad rows.  Index arithmetic is 32-bit (tt_create caps
@@ -24,7 +25,8 @@ __device__ __forceinline__ void store4(S *p, float a, float b, float c, float d)
 }
 
 template <typename T, typename S>
-__global__ void k_pack(const T *__restrict__ c, S *__restrict__ cpad, int nx, int ny, int nz, int K, int KP)
+__global__ void k_pack(const T *__restrict__ c, S *__restrict__ cpad, S *__restrict__ cpadx, int nx, int ny, int nz,
+                       int K, int KP)
 {
     const int QP = KP / 4;
     const int n = nx * ny * nz * QP;
@@ -36,11 +38,17 @@ __global__ void k_pack(const T *__restrict__ c, S *__restrict__ cpad, int nx, in
 #pragma unroll
         for (int i = 0; i < 4; ++i) val[i] = i0 + i < K ? __ldg(src + i0 + i) : T(0);
         S *dst = cpad + (((long long)(x + 2) * (ny + 4) + (y + 2)) * (nz + 4) + (z + 2)) * KP + i0;
+        S *dstx = cpadx ? cpadx + (((long long)(z + 2) * (ny + 4) + (y + 2)) * (nx + 4) + (x + 2)) * KP + i0 : nullptr;
         if constexpr (std::is_same<T, double>::value) {
             reinterpret_cast<double2 *>(dst)[0] = make_double2(val[0], val[1]);
             reinterpret_cast<double2 *>(dst)[1] = make_double2(val[2], val[3]);
+            if (dstx) {
+                reinterpret_cast<double2 *>(dstx)[0] = make_double2(val[0], val[1]);
+                reinterpret_cast<double2 *>(dstx)[1] = make_double2(val[2], val[3]);
+            }
         } else {
             store4<S>(dst, val[0], val[1], val[2], val[3]);
+            if (dstx) store4<S>(dstx, val[0], val[1], val[2], val[3]);
         }
     }
 }
@@ -71,7 +79,8 @@ cudaError_t launch_pack(tt_handle *h, const T *c)
 {
     cudaEvent_t ev;
     prof_begin(h, TT_KSLOT_PACK, &ev);
-    k_pack<T, S><<<grid_for(h->nvox() * h->KP / 4), 256, 0, h->stream>>>(c, (S *)h->cpad, h->N[0], h->N[1],
+    S *cpadx = h->xcopy ? (S *)h->cpad + h->pad_vox * h->KP : nullptr;
+    k_pack<T, S><<<grid_for(h->nvox() * h->KP / 4), 256, 0, h->stream>>>(c, (S *)h->cpad, cpadx, h->N[0], h->N[1],
                                                                        h->N[2], h->K, h->KP);
     cudaError_t e = cudaGetLastError();
     prof_end(h, TT_KSLOT_PACK, ev);

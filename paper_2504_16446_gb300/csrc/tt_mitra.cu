@@ -71,9 +71,10 @@ __global__ void k_abs_sums(const double *__restrict__ B, int S, int C, int K, in
     }
 }
 
-// Interior of the padded volume: channel 0 = 1, the others 0.
+// Interior of the padded volume (and of its x-innermost copy cpadx, if any):
+// channel 0 = 1, the others 0.
 template <typename S>
-__global__ void k_unit_volume(S *__restrict__ cpad, int nx, int ny, int nz, int KP)
+__global__ void k_unit_volume(S *__restrict__ cpad, S *__restrict__ cpadx, int nx, int ny, int nz, int KP)
 {
     const long long n = (long long)nx * ny * nz * KP;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
@@ -83,6 +84,7 @@ __global__ void k_unit_volume(S *__restrict__ cpad, int nx, int ny, int nz, int 
         const int z = (int)(v % nz), y = (int)((v / nz) % ny), x = (int)(v / ((long long)nz * ny));
         const long long o = (((long long)(x + 2) * (ny + 4) + (y + 2)) * (nz + 4) + (z + 2)) * KP + i;
         cpad[o] = S(i == 0 ? 1.0f : 0.0f);
+        if (cpadx) cpadx[(((long long)(z + 2) * (ny + 4) + (y + 2)) * (nx + 4) + (x + 2)) * KP + i] = S(i == 0 ? 1.0f : 0.0f);
     }
 }
 
@@ -151,8 +153,8 @@ tt_status sirt_weights_impl(tt_handle *h, const T *W, T *R, T *D)
     prof_begin(h, TT_KSLOT_VECTOR, &ev);
     k_abs_sums<<<blocks_for((long long)h->S * (h->C + h->KP)), 256, 0, h->stream>>>(h->B64, h->S, h->C, h->K, h->KP,
                                                                                  row_abs, col_abs);
-    k_unit_volume<S><<<blocks_for(h->nvox() * h->KP), 256, 0, h->stream>>>((S *)h->cpad, h->N[0], h->N[1], h->N[2],
-                                                                        h->KP);
+    k_unit_volume<S><<<blocks_for(h->nvox() * h->KP), 256, 0, h->stream>>>(
+        (S *)h->cpad, h->xcopy ? (S *)h->cpad + h->pad_vox * h->KP : nullptr, h->N[0], h->N[1], h->N[2], h->KP);
     e = cudaGetLastError();
     prof_end(h, TT_KSLOT_VECTOR, ev);
     if (e == cudaSuccess) e = launch_forward<T, S>(h, R, nullptr, nullptr, false);

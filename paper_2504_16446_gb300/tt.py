@@ -107,6 +107,7 @@ SIGNATURES = {
                                            ctypes.c_double, ctypes.c_double, _D]),
     "tt_wsnet_get_weights": (ctypes.c_int, [_P, _P]),
     "tt_conv3d_bf16": (ctypes.c_int, [ctypes.c_int] * 5 + [_P, _P, ctypes.c_int, _P, _P]),
+    "tt_conv3d_bf16_act": (ctypes.c_int, [ctypes.c_int] * 5 + [_P, _P, ctypes.c_int, _P, _P]),
     "tt_conv3d_wgrad_bf16": (ctypes.c_int, [ctypes.c_int] * 5 + [_P, _P, _P, _P]),
     "tt_umma_gemm_bf16": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "tt_zonal_to_sh": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, _P, _P, _P, _P]),

@@ -57,6 +57,45 @@ def test_conv_kernels_match_oracle(cin, cout, shape):
     assert rel_l2(dw.cpu().numpy(), dw_ref.reshape(27, cout, cin)) <= 1e-5
 
 
+@pytest.mark.parametrize("cin,cout,relu", [(16, 32, 1), (32, 32, 1), (32, 32, 0), (32, 16, 0), (16, 32, 0)])
+@pytest.mark.parametrize("shape", [(5, 7, 37), (9, 3, 20)])
+def test_hidden_layer_form_matches_oracle(cin, cout, relu, shape):
+    """bfloat16 output (ReLU fused or not), the network's hidden layers: each
+    element is the FP32 accumulation rounded once to bfloat16, so it is
+    within one bfloat16 unit (at most 2^-7 relative, plus the FP32 sum's
+    error near zero) of the oracle's FP64 value rounded the same way, and
+    within 2^-8 relative L2 (half a unit) of the unrounded one."""
+    rng = np.random.default_rng(cin + 3 * cout + relu + shape[2])
+    x = bf16_round(rng.normal(size=shape + (cin,)))
+    w = bf16_round(rng.normal(size=(27, cout, cin)) * 0.2)
+    lib = tt.load()
+    xd = torch.as_tensor(bf16_bits(x).view(np.int16), device="cuda")
+    wd = torch.as_tensor(bf16_bits(w).view(np.int16), device="cuda")
+    y = torch.full(shape + (cout,), -1, dtype=torch.int16, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.tt_conv3d_bf16_act(*shape, cin, cout, xd.data_ptr(), wd.data_ptr(), relu, y.data_ptr(), s) == 0
+    got = (y.cpu().numpy().view(np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    ref = conv3d(x, w.reshape(3, 3, 3, cout, cin))
+    if relu:
+        ref = np.maximum(ref, 0.0)
+    ref_b = bf16_round(ref)
+    # one bfloat16 unit (at most 2^-7 of the value: 8 significant bits),
+    # plus the FP32 accumulation's own error near zero
+    assert np.all(np.abs(got - ref_b) <= 2.0 ** -7 * np.abs(ref_b) + 1e-5 * np.abs(ref).max())
+    assert rel_l2(got, ref) <= 2.0 ** -8
+    if relu:
+        assert np.all(got >= 0.0)
+
+
+def test_hidden_layer_form_rejects_uncompiled_pairs():
+    lib = tt.load()
+    x = torch.zeros((2, 2, 2, 16), dtype=torch.int16, device="cuda")
+    w = torch.zeros((27, 16, 16), dtype=torch.int16, device="cuda")
+    y = torch.zeros((2, 2, 2, 16), dtype=torch.int16, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.tt_conv3d_bf16_act(2, 2, 2, 16, 16, x.data_ptr(), w.data_ptr(), 0, y.data_ptr(), s) == tt.TT_UNSUPPORTED
+
+
 def test_network_gradient_matches_oracle():
     k_in, k_out = 15, 15
     shape = (6, 5, 21)
