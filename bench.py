@@ -59,6 +59,10 @@ def parse():
                     help="L-BFGS iterations of the reference solve that defines L*")
     ap.add_argument("--cpu-sample-evals", type=float, default=4.0,
                     help="oracle sample size in full-workload gradient evaluations")
+    ap.add_argument("--ws-test", type=int, default=8,
+                    help="held-out 128^3 phantoms of the warm-start time-to-loss comparison (0: skip)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the FP64 cylinder and plywood composite-loss workloads")
     return ap.parse_args()
 
 
@@ -500,6 +504,188 @@ def measure_forms(torch, tt, synth, flush, steps: int = 20):
     return res
 
 
+def _timed(torch, fn, flush, steps):
+    """Mean device ms of fn() over steps calls (L2 flushed before each), after 3 warm-up calls."""
+    for _ in range(3):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / steps
+
+
+def config_inputs(name, torch, tt, synth, h, noise, seed):
+    """(I, c_true) of a named workload: its phantom's SH coefficients (GPU
+    kernel), forward-projected on the GPU, with the workload's noise
+    ("gauss": sigma = 1% of the mean; ("poisson", mean counts))."""
+    st = h.setup
+    ph = synth.phantom(name)
+    dt = h.dtype
+    dirs = torch.as_tensor(ph.dirs.reshape(-1, 3), dtype=torch.float32, device="cuda")
+    amps = torch.as_tensor(ph.amps.reshape(-1, st.ell_max // 2 + 1), dtype=torch.float32, device="cuda")
+    c_true = tt.zonal_to_sh(st.ell_max, dirs, amps).reshape(st.volume_shape).to(dt).contiguous()
+    clean = h.project(c_true)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    if noise == "gauss":
+        I = clean + 0.01 * float(clean.mean()) * torch.randn(clean.shape, device="cuda", dtype=dt, generator=gen)
+    else:
+        scale = noise[1] / float(clean.mean())
+        I = torch.poisson(clean.clamp(min=0).float() * scale, generator=gen).to(dt) / scale
+    return I.contiguous(), c_true
+
+
+def measure_configs(torch, tt, synth, flush):
+    """The FP64 cylinder workload (one gradient evaluation and a 20-step
+    L-BFGS solve on an FP64 handle) and the plywood composite loss (squared +
+    1e-3 L2 + 1e-2 Huber-TV through the autograd front end, forward and
+    backward per evaluation, with the regularisers' share)."""
+    from paper_2504_16446_gb300 import autograd as ta
+    out = {}
+    # 16^3, l_max 2, 30 projections of 16x16 x 8 segments, FP64
+    st = synth.workload("cyl16")
+    h = tt.Handle(st, "f64")
+    I, c_true = config_inputs("cyl16", torch, tt, synth, h, "gauss", 0)
+    z = torch.zeros(st.volume_shape, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(z)
+    ms_eval = _timed(torch, lambda: h.gradient_residual(z, I, None, out=g), flush, 50)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    opt = tt.LBFGS(h, z, I, None, m=10, log=False)
+    L0 = opt.loss
+    iters, evals = 0, 1
+    for _ in range(20):
+        _, ne, status = opt.step()
+        iters += 1
+        evals += ne
+        if status != tt.TT_OK:
+            break
+    torch.cuda.synchronize()
+    solve = time.perf_counter() - t0
+    out["cyl16_f64"] = {"workload": "16^3, l_max 2 (K=6), 30 projections (15 rotations x tilts 0, 30 deg) of 16x16 "
+                                    "x 8 segments, cylinder phantom, Gaussian noise 1% of the mean, FP64",
+                        "ms_per_eval": ms_eval, "evals_per_s": 1e3 / ms_eval,
+                        "lbfgs_20": {"seconds": solve, "iterations": iters, "evals": evals,
+                                     "loss_ratio": opt.loss / L0}}
+    opt.close()
+    h.close()
+    # 100^3, l_max 6, 180 projections of 100x100 x 8 segments, composite loss through autograd
+    st = synth.workload("ply100")
+    h = tt.Handle(st, "f32")
+    I, c_true = config_inputs("ply100", torch, tt, synth, h, ("poisson", 5e3), 3)
+    c = (0.5 * c_true).contiguous()
+
+    def composite():
+        x = c.detach().requires_grad_(True)
+        L = ta.squared_loss(h, x, I) + 1e-3 * ta.l2_norm(h, x) + 1e-2 * ta.tv_huber(h, x, 1e-2)
+        L.backward()
+        return L
+
+    def regularisers():
+        x = c.detach().requires_grad_(True)
+        L = 1e-3 * ta.l2_norm(h, x) + 1e-2 * ta.tv_huber(h, x, 1e-2)
+        L.backward()
+        return L
+
+    ms_comp = _timed(torch, composite, flush, 10)
+    ms_reg = _timed(torch, regularisers, flush, 10)
+    out["ply100_composite"] = {"workload": "100^3, l_max 6 (K=28), 180 projections (45 rotations x 4 tilts) of "
+                                           "100x100 x 8 segments, plywood phantom, Poisson counts at mean 5e3, FP32",
+                               "loss": "squared + 1e-3 L2 + 1e-2 Huber-TV (delta 1e-2), torch.autograd forward + "
+                                       "backward",
+                               "ms_per_eval": ms_comp, "evals_per_s": 1e3 / ms_comp,
+                               "regularisers_ms": ms_reg, "regulariser_share": ms_reg / ms_comp}
+    h.close()
+    return out
+
+
+def config_oracle_legs(torch, tt, synth):
+    """CPU-baseline leg of the cylinder and plywood workloads: the FP64 oracle
+    timed on one gradient evaluation (the whole cylinder workload; three
+    plywood projections), and the GPU's relative error against it on the same
+    seeded inputs (random volume and data from the input generators)."""
+    import numpy as np
+    import oracle
+    from oracle.regularizers import l2_norm as or_l2, tv_huber as or_tv
+    from paper_2504_16446_gb300 import autograd as ta
+
+    def geom(st):
+        return oracle.Geometry(st.shape, st.nj, st.nk, st.ell_max, st.inner_angle, st.outer_angle, st.seg_start,
+                               st.seg_end, j_offset=st.j_offset, k_offset=st.k_offset, two_theta=st.two_theta,
+                               a=st.a, b=st.b)
+
+    def rel(a, b):
+        return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+    out = {}
+    st = synth.workload("cyl16")
+    c = synth.random_volume(st, 31)
+    I = synth.random_data(st, 32)
+    g_or = geom(st)
+    B = oracle.basis_matrix(g_or)
+    t0 = time.perf_counter()
+    L_ref, g_ref = oracle.gradient_residual(g_or, c, I, None, B)
+    t_or = time.perf_counter() - t0
+    h = tt.Handle(st, "f64")
+    L, g = h.gradient_residual(torch.as_tensor(c, device="cuda"), torch.as_tensor(I, device="cuda"))
+    out["cyl16_f64"] = {"oracle_s_per_eval": t_or, "oracle_cores": 1, "loss_rel_err": abs(L - L_ref) / abs(L_ref),
+                        "grad_rel_l2": rel(g.cpu().numpy(), g_ref), "tolerance": 1e-12,
+                        "inputs": "random volume N(0,1) seed 31, random data N(0,1) seed 32"}
+    h.close()
+    st = synth.workload("ply100").subset([0, 61, 133])
+    c = synth.random_volume(st, 33).astype(np.float32)
+    I = (synth.random_data(st, 34) + 100.0).astype(np.float32)
+    g_or = geom(st)
+    c64, I64 = c.astype(np.float64), I.astype(np.float64)
+    t0 = time.perf_counter()
+    lr, gr = oracle.gradient_residual(g_or, c64, I64)
+    l2v, l2g = or_l2(c64)
+    tvv, tvg = or_tv(c64, 1e-2)
+    t_or = time.perf_counter() - t0
+    L_ref, g_ref = lr + 1e-3 * l2v + 1e-2 * tvv, gr + 1e-3 * l2g + 1e-2 * tvg
+    h = tt.Handle(st, "f32")
+    x = torch.as_tensor(c, device="cuda").requires_grad_(True)
+    L = ta.squared_loss(h, x, torch.as_tensor(I, device="cuda")) + 1e-3 * ta.l2_norm(h, x) + \
+        1e-2 * ta.tv_huber(h, x, 1e-2)
+    L.backward()
+    out["ply100_composite"] = {"oracle_s_per_eval_3_projections": t_or, "oracle_cores": 1,
+                               "loss_rel_err": abs(L.item() - L_ref) / abs(L_ref),
+                               "grad_rel_l2": rel(x.grad.cpu().numpy(), g_ref), "tolerance": 1e-5,
+                               "inputs": "projections 0, 61, 133; random volume N(0,1) seed 33, data 100 + N(0,1) "
+                                         "seed 34"}
+    h.close()
+    return out
+
+
+def warm_start_time_to_loss(torch, tt, n_test: int, ref_iters: int):
+    """The plain FP32 form against the mixed-precision, warm-started form:
+    L-BFGS time to (L - L*)/(L0 - L*) <= 1e-3 from zero (FP32 handle) and from
+    the learned warm start (bfloat16-storage handle; inference and the three
+    loss evaluations that scale the prediction included) on held-out 128^3
+    phantoms (l_max 4, 240 projections of 128x128 x 16 segments).  The
+    network's weights come from the file that the training script writes
+    (``python -m paper_2504_16446_gb300.warmstart --save-weights``); without
+    it, a smaller network is trained in this run (48 phantoms)."""
+    from paper_2504_16446_gb300 import warmstart
+    if os.path.exists(warmstart.WEIGHTS):
+        net = warmstart.load_net()
+        src = ("weights file " + os.path.relpath(warmstart.WEIGHTS, ROOT) + " written by python -m "
+               "paper_2504_16446_gb300.warmstart --save-weights (512 training phantoms of the 64^3 workload)")
+    else:
+        net, info = warmstart.train(48, 6, 40)
+        src = f"trained in this run: 48 phantoms of the 64^3 workload, 40-iteration targets ({info['data_seconds'] + info['train_seconds']:.1f} s)"
+    summary, _ = warmstart.held_out_test(net, n_test, ref_iters)
+    net.close()
+    summary["weights"] = src
+    return summary
+
+
 def run_ours(args):
     import torch
     from paper_2504_16446_gb300 import build, synth, tt
@@ -596,6 +782,8 @@ def run_ours(args):
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     # FP32 FMA peak: 128 lanes per SM, 2 flops per FMA, at the median SM clock under load
     fp32_peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    l1_peak = sm_count * 128 * sm_mhz * 1e6 / 1e9           # GB/s, L1 / shared memory to registers
+    tap_bytes = st.S * st.nj * st.nk * st.shape[0] * 4 * st.K * 4
     kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / max(1e-12, sum(x[0] for x in prof.values()))}
                for k, v in prof.items() if v[1]}
 
@@ -613,6 +801,13 @@ def run_ours(args):
                      "step_frac": 2 * sweep_bytes / (ms_per_step * 1e-3) / 1e9 / peak},
         # t_roof = max(compulsory HBM bytes / HBM peak, FP32 flops / FP32 peak) against the step time
         "binding_roof": binding_roof(st, ms_per_step, peak, fp32_peak),
+        # the path the projector kernels saturate: bilinear taps delivered from
+        # L1 / shared memory to registers, 4 taps x K channels x 4 B per
+        # (ray, plane) in either direction, against 128 B per clock per SM
+        "l1_roof": {k: {"achieved_gbs": tap_bytes / (prof[k][0] / prof[k][1] * 1e-3) / 1e9, "peak_gbs": l1_peak,
+                        "frac": tap_bytes / (prof[k][0] / prof[k][1] * 1e-3) / 1e9 / l1_peak,
+                        "bytes_per_launch": tap_bytes}
+                    for k in ("forward", "adjoint") if prof[k][1]},
         "fp32_alu": {"kernel": dom, "achieved_tflops": flops / (dom_ms * 1e-3) / 1e12,
                      "peak_tflops": fp32_peak, "frac": flops / (dom_ms * 1e-3) / 1e12 / fp32_peak,
                      "peak_formula": "sm_count x 128 lanes x 2 flops x median SM clock"},
@@ -633,7 +828,15 @@ def run_ours(args):
         hb.close()
         out["time_to_loss"]["sirt_weighted"] = mitra_vs_lbfgs(h, I, W, torch, tt, args.ttl_ref_iters)
         out["time_to_loss"]["noise_free"] = noise_free_residual(h, c_true, torch, tt)
+        if args.ws_test > 0:
+            ws = warm_start_time_to_loss(torch, tt, args.ws_test, 150)
+            for key in ("zero_f32", "warm_bf16"):
+                out["time_to_loss"][key] = dict(ws[key], samples=ws["samples"], workload=ws["workload"],
+                                                criterion=ws["criterion"])
+            out["time_to_loss"]["warm_start"] = ws
     out["standalone"] = standalone(h, c, I, torch, flush)
+    if not args.no_configs:
+        out["configs"] = measure_configs(torch, tt, synth, flush)
     if not args.no_forms:
         out["forms"] = measure_forms(torch, tt, synth, flush)
         out["paper_shaped"] = paper_shaped(torch, tt, synth, flush)
@@ -645,6 +848,9 @@ def run_ours(args):
         rate, dt, used, sample = cpu_oracle_rate_cores(st, cn, In, Wn, reps, procs)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
                                "single_core": {"value": rate1, "cores": 1, "sample": sample1}}
+        if not args.no_configs:
+            for k, v in config_oracle_legs(torch, tt, synth).items():
+                out.setdefault("configs", {}).setdefault(k, {})["oracle"] = v
     if dist:
         dist.barrier()
         dist.destroy_process_group()
