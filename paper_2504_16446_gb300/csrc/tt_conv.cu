@@ -10,6 +10,7 @@
 //   y[v][co] = sum_t sum_ci a[v + d_t][ci] * wk[t][co][ci].
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -71,9 +72,10 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
 // (y, z) tile column.  Tile x needs planes x-1, x, x+1 from a ring of four
 // plane buffers, so each step stages one new plane.  Step for tile x: one
 // thread issues its MMAs into tensor-memory accumulator x % 2 and commits
-// them to mbarrier x % 2; while they run, all eight warps wait for tile
-// x-1's mbarrier, write tile x-1 out (ReLU, bf16 or f32), and stage plane
-// x+2 into the buffer that tile x-1 was the last to read.  A wait that gives
+// them to mbarrier x % 2; while they run, all eight warps issue the global
+// loads of plane x+3 into registers, wait for tile x-1's mbarrier, write tile
+// x-1 out (ReLU, bf16 or f32), and store plane x+2 -- loaded a step earlier
+// -- into the buffer that tile x-1 was the last to read.  A wait that gives
 // up writes NaN into its tile, which every consumer of the output sees.
 constexpr uint32_t kTcWaitTries = 1u << 22;
 constexpr int kTcThreads = 256;
@@ -198,7 +200,7 @@ __device__ __forceinline__ void tile_epilogue(uint32_t tmem, uint32_t acc_col, b
 template <int CIN, int COUT, bool RELU, bool OUT_F32>
 __global__ void __launch_bounds__(kTcThreads)
 k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ wk, void *__restrict__ out,
-                int nx, int ny, int nz, int tiles_y, int tiles_z, int seg_len, int segs_x, int n_units)
+                int nx, int ny, int nz, int tiles_y, int tiles_z)
 {
     using L = TcConvSmem<CIN, COUT>;
     constexpr int KC = CIN / 8, NB = 3 * COUT;
@@ -225,13 +227,22 @@ k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__res
     const uint32_t s_planes = umma::smem_u32(smem), s_wts = umma::smem_u32(smem + L::wts);
     uint32_t issued[2] = {0, 0};          // tiles waited per mbarrier (parity of the next wait)
 
-    for (int unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
-        const int sx = unit % segs_x, tz = (unit / segs_x) % tiles_z, ty = unit / (segs_x * tiles_z);
-        const int y0 = ty * 4, z0 = tz * kTileZ, xa = sx * seg_len;
-        const int xb = min(nx, xa + seg_len);
-        // planes xa-1, xa, xa+1 before the first tile (the ring is idle here)
+    // This CTA's equal share [t_begin, t_end) of the tile sequence (x fastest,
+    // then the z tile, then the y tile), walked as runs of consecutive x.
+    const long long n_tiles = (long long)nx * tiles_y * tiles_z;
+    const long long t_begin = n_tiles * blockIdx.x / gridDim.x, t_end = n_tiles * (blockIdx.x + 1) / gridDim.x;
+    for (long long t = t_begin; t < t_end;) {
+        const long long col = t / nx;
+        const int tz = (int)(col % tiles_z), ty = (int)(col / tiles_z);
+        const int y0 = ty * 4, z0 = tz * kTileZ, xa = (int)(t - col * nx);
+        const int xb = (int)std::min<long long>(nx, xa + (t_end - t));
+        t += xb - xa;
+        // planes xa-1, xa, xa+1 before the first tile (the ring is idle here);
+        // plane xa+2's loads go out now and are stored during the first step
         for (int px = xa - 1; px <= xa + 1; ++px)
             stage_plane<CIN>(smem + (px & 3) * L::plane, in, px, y0, z0, nx, ny, nz, tid);
+        PlaneRegs<CIN> next;
+        if (xa + 2 <= xb) plane_load<CIN>(next, in, xa + 2, y0, z0, nx, ny, nz, tid);
         for (int x = xa; x <= xb; ++x) {
             const int i = x - xa;                 // step: tile x issued, tile x-1 written out, plane x+2 staged
             umma::fence_async_smem();
@@ -251,12 +262,12 @@ k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__res
                 }
                 umma::mma_commit(mbar + (i & 1));
             }
-            // plane x+2 (for tile x+1): its loads go out now, overlapping the
-            // running MMAs and tile x-1's write-out; the stores wait until the
-            // MMAs of tile x-1, the last reader of that ring buffer, are done
-            PlaneRegs<CIN> next;
-            const bool stage = x + 2 <= xb;
-            if (stage) plane_load<CIN>(next, in, x + 2, y0, z0, nx, ny, nz, tid);
+            // Plane x+3's loads go out now and stay in registers for a whole
+            // step; plane x+2 (for tile x+1), loaded one step ago, is stored
+            // once the MMAs of tile x-1, the last reader of that ring buffer,
+            // are done.
+            PlaneRegs<CIN> after;
+            if (x + 3 <= xb) plane_load<CIN>(after, in, x + 3, y0, z0, nx, ny, nz, tid);
             if (i > 0) {
                 const int p = (i - 1) & 1;
                 const bool ok = umma::mbar_wait(mbar + p, issued[p] & 1u, kTcWaitTries);
@@ -265,10 +276,11 @@ k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__res
                 tile_epilogue<COUT, RELU, OUT_F32>(tmem, (uint32_t)(NB * p), ok, out, x - 1, y0, z0, ny, nz, warp,
                                                    lane);
             }
-            if (stage) {
+            if (x + 2 <= xb) {
                 umma::fence_async_smem();
                 plane_store<CIN>(smem + ((x + 2) & 3) * L::plane, next, tid);
             }
+            next = after;
         }
         umma::fence_before_sync();
         __syncthreads();                       // ring and accumulators free for the next run
@@ -465,9 +477,11 @@ static unsigned grid_n(long long n)
 }
 
 // Launches the forward convolution (tcgen05 kernel) for a (CIN, COUT) pair:
-// persistent CTAs (two per SM when the staging fits) over runs of seg_len x
-// planes; runs of 16 planes, shortened (to no fewer than 4) while there are
-// fewer than two runs per CTA.
+// persistent CTAs (two per SM when the staging fits), each walking an equal
+// contiguous share of the nx * tiles_y * tiles_z tiles (x fastest) as runs
+// of consecutive x planes (measured at 128^3, 32 -> 32 channels: runs of 16
+// planes dealt round robin left a 19% tail; equal shares cut it and the
+// pipeline fills to about 1.5 runs per CTA).
 cudaError_t conv3d_forward(const __nv_bfloat16 *in, const __nv_bfloat16 *wk, void *out, int nx, int ny, int nz, int cin,
                            int cout, bool relu, bool out_f32, cudaStream_t st)
 {
@@ -479,12 +493,10 @@ cudaError_t conv3d_forward(const __nv_bfloat16 *in, const __nv_bfloat16 *wk, voi
         constexpr uint32_t sm = TcConvSmem<CI, CO>::bytes > 80u * 1024u ? TcConvSmem<CI, CO>::bytes   \
                                                                         : 80u * 1024u;                 \
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);             \
-        const int slots = sm_count() * (sm <= 110u * 1024u ? 2 : 1);                                  \
-        int seg = 16;                                                                                 \
-        while (seg > 4 && ((nx + seg - 1) / seg) * tiles_y * tiles_z < 2 * slots) seg /= 2;           \
-        const int segs_x = (nx + seg - 1) / seg, n_units = segs_x * tiles_y * tiles_z;                \
-        const int grid = n_units < slots ? n_units : slots;                                           \
-        kern<<<grid, kTcThreads, sm, st>>>(in, wk, out, nx, ny, nz, tiles_y, tiles_z, seg, segs_x, n_units); \
+        const long long slots = (long long)sm_count() * (sm <= 110u * 1024u ? 2 : 1);                  \
+        const long long n_tiles = (long long)nx * tiles_y * tiles_z;                                   \
+        const int grid = (int)(n_tiles < slots ? n_tiles : slots);                                     \
+        kern<<<grid, kTcThreads, sm, st>>>(in, wk, out, nx, ny, nz, tiles_y, tiles_z);                \
         return cudaGetLastError();                                                                    \
     } while (0)
     if (nx < 1 || ny < 1 || nz < 1) return cudaSuccess;
