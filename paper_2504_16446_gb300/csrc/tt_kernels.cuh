@@ -37,7 +37,22 @@ __device__ __forceinline__ void fma2(float &a0, float &a1, float w, float x0, fl
 template <typename T, int CPL>
 __device__ __forceinline__ void fma_row(T (&acc)[CPL], T w, const T *__restrict__ p)
 {
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4 && CPL % 8 == 0) {
+        // whole 32-byte pieces of a row (the row and the lane's chunk start
+        // on 32-byte boundaries): 256-bit loads (100^3, l_max 6 adjoint, 8
+        // floats per lane: 4.02 -> 3.80 ms against 16-byte loads)
+#pragma unroll
+        for (int t = 0; t < CPL / 8; ++t) {
+            unsigned x[8];
+            asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                         : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]),
+                           "=r"(x[7])
+                         : "l"(p + 8 * t));
+#pragma unroll
+            for (int i = 0; i < 8; i += 2)
+                fma2(acc[8 * t + i], acc[8 * t + i + 1], w, __uint_as_float(x[i]), __uint_as_float(x[i + 1]));
+        }
+    } else if constexpr (sizeof(T) == 4) {
         static_assert(CPL % 4 == 0, "float rows are read as float4");
 #pragma unroll
         for (int t = 0; t < CPL / 4; ++t) {
@@ -875,6 +890,9 @@ cudaError_t launch_adjoint_L(tt_handle *h, T *g, bool reduce_loss)
 {
     // For K <= 8 a single lane owns a voxel and reads its whole (32-byte) G
     // row: no candidate exchange, measured 7% faster than two-lane groups.
+    // (one lane per voxel for K = 15 as well was measured 0.37 -> 0.50 ms
+    // at 64^3: the lane's 16 channels cost the shared weight exchange's
+    // savings back in wavefronts)
     constexpr int K = num_coeffs(L), KP = padded_k(K), LG = K <= 8 ? 1 : lane_group(K), V = adjoint_voxels(KP, LG);
     constexpr int GZ = adjoint_gz(LG), BXT = (kThreads / 32 / 4) * (32 / LG / GZ) * V, BY = 4;
     const int tx = (h->N[0] + BXT - 1) / BXT, ty = (h->N[1] + BY - 1) / BY, tz = (h->N[2] + GZ - 1) / GZ;

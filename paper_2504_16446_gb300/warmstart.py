@@ -199,13 +199,17 @@ def held_out_test(net: tt.WarmStartNet, n_test: int = 32, ref_iters: int = 150, 
     h32 = tt.Handle(st, "f32")
     h16 = tt.Handle(st, "bf16")
     z = torch.zeros(st.volume_shape, dtype=torch.float32, device="cuda")
-    # one untimed inference first: the network's first call in a process
-    # loads its kernels and sets their shared-memory limits (reported apart)
+    # one untimed warm start first, on the first test phantom: the first
+    # call in a process loads kernels and grows the allocator's pools
+    # (reported apart from the per-phantom times)
+    I, _ = phantom_data(h32, st, 6, seed0)
+    L0, g0 = h32.gradient_residual(z, I, None)
     torch.cuda.synchronize()
     t_first = time.perf_counter()
-    net.forward(torch.ones((st.shape[0], st.shape[1], st.shape[2], 15), dtype=torch.float32, device="cuda"), 1.0, 1.0)
+    warm_start(net, h32, I, g0, L0)
     torch.cuda.synchronize()
     t_first = time.perf_counter() - t_first
+    del I, g0
     rows = []
     for s in range(n_test):
         I, _ = phantom_data(h32, st, 6, seed0 + s)
@@ -239,7 +243,7 @@ def held_out_test(net: tt.WarmStartNet, n_test: int = 32, ref_iters: int = 150, 
                "warm_bf16": {"iterations": agg("warm_bf16", 0), "evals": agg("warm_bf16", 1),
                              "seconds": agg("warm_bf16", 2) + t_ws, "warm_start_seconds": t_ws},
                "fewer_iterations_in": int(sum(r["warm_bf16"][0] < r["zero_f32"][0] for r in rows)),
-               "first_inference_seconds": t_first}
+               "first_call_seconds": t_first}
     return summary, rows
 
 
