@@ -11,8 +11,9 @@ and the judge: the warm start is used only if its loss is below L(0).
 Scale: the network is bias-free and ReLU is positively homogeneous, so the
 input is normalised by its RMS and the output scale is fixed at inference by
 the exact minimiser of the loss along the predicted direction u:
-L(alpha u) = alpha^2 |Au|^2 - 2 alpha <Au, I> + |I|^2 (W = 1), whose three
-coefficients follow from the library's loss at 0, u and 2u.
+L(alpha u) = alpha^2 |Au|^2 - 2 alpha <Au, I> + L(0), whose coefficients
+follow from the library's loss at 0, u and 2u (the loss at the minimiser is
+then known too).
 
 Running this module (``python -m paper_2504_16446_gb300.warmstart``) trains
 on the 64^3 ellipsoid workload and tests on held-out 128^3 phantoms (l_max 4,
@@ -65,7 +66,9 @@ def plain_solve(h: tt.Handle, I, iters: int, c0=None):
 
 def warm_start(net: tt.WarmStartNet, h: tt.Handle, I, g0, L0: float):
     """(c0, loss): alpha * net(g0 / rms(g0)) with the loss-minimising alpha, or
-    zero when that does not beat L(0)."""
+    zero when that does not beat L(0).  Along u the loss is the quadratic
+    L(alpha u) = alpha^2 |Au|^2 - 2 alpha <Au, I> + L0, so L(u) and L(2u) fix
+    it and its minimum L0 - <Au, I>^2 / |Au|^2 is the loss at c0."""
     s_in = float(g0.pow(2).mean().sqrt())
     u = net.forward(g0, s_in, 1.0).contiguous()
     L1, _ = h.gradient_residual(u, I, None, want_grad=False)
@@ -74,11 +77,10 @@ def warm_start(net: tt.WarmStartNet, h: tt.Handle, I, g0, L0: float):
     lin = 0.5 * (L0 + quad - L1)               # <Au, I>
     if not quad > 0:
         return torch.zeros_like(u), L0
-    c0 = ((lin / quad) * u).contiguous()
-    Lw, _ = h.gradient_residual(c0, I, None, want_grad=False)
-    if Lw >= L0:
+    Lw = L0 - lin * lin / quad
+    if not Lw < L0:
         return torch.zeros_like(u), L0
-    return c0, Lw
+    return ((lin / quad) * u).contiguous(), Lw
 
 
 def iterations_to(h: tt.Handle, I, c0, L0: float, Lstar: float, target: float, max_iter: int):
@@ -193,7 +195,7 @@ def held_out_test(net: tt.WarmStartNet, n_test: int = 32, ref_iters: int = 150, 
     (l_max 4, 240 projections of 128 x 128 x 16 segments; L* = plain FP32
     L-BFGS after ref_iters iterations): zero-start FP32, warm-started FP32 and
     warm-started bfloat16-storage solves.  The warm rows' seconds include the
-    inference and the three loss evaluations that scale it.  Returns
+    inference and the two loss evaluations that scale it.  Returns
     (summary, per-sample rows)."""
     st = synth.workload("ell128c16")
     h32 = tt.Handle(st, "f32")
