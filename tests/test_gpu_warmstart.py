@@ -201,3 +201,25 @@ def test_warm_start_gains_over_zero_start():
           "L(c0)/L(0)", [round(r, 4) for r in loss_ratio])
     assert max(loss_ratio) < 0.5
     assert sum(iters_warm) < sum(iters_zero)
+
+
+def test_warm_start_scaling_reports_the_loss_at_its_result():
+    """warmstart.warm_start scales the network's output u by the exact
+    minimiser of the loss along it, from the losses at u and 2u (the squared
+    loss is a quadratic in the scale); the loss it reports for the scaled
+    start equals the library's loss there, and lies below L(0)."""
+    from paper_2504_16446_gb300 import warmstart
+    st = synth.small_setup(n=(16, 16, 16), nj=16, nk=16, ell_max=4, n_proj=12, n_seg=8, seed=21, offsets=False)
+    h = tt.Handle(st, "f32")
+    ph = synth.ellipsoid_phantom(16, 4, 3, 77)
+    dirs = torch.as_tensor(ph.dirs.reshape(-1, 3), dtype=torch.float32, device="cuda")
+    amps = torch.as_tensor(ph.amps.reshape(-1, 3), dtype=torch.float32, device="cuda")
+    c_true = tt.zonal_to_sh(4, dirs, amps).reshape(st.volume_shape).contiguous()
+    I = h.project(c_true)
+    z = torch.zeros(st.volume_shape, dtype=torch.float32, device="cuda")
+    L0, g0 = h.gradient_residual(z, I, None)
+    net = tt.WarmStartNet(15, 15, seed=5)
+    c0, Lw = warmstart.warm_start(net, h, I, g0, L0)
+    assert float(c0.abs().max()) > 0 and Lw < L0
+    L_true, _ = h.gradient_residual(c0, I, None, want_grad=False)
+    assert abs(L_true - Lw) <= 1e-4 * L0
