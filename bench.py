@@ -63,6 +63,8 @@ def parse():
                     help="held-out 128^3 phantoms of the warm-start time-to-loss comparison (0: skip)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the FP64 cylinder and plywood composite-loss workloads")
+    ap.add_argument("--forward-kernel", choices=["auto", "l1", "staged"], default="auto",
+                    help="forward-projection kernel of the timed handle (tt_set_forward_kernel)")
     return ap.parse_args()
 
 
@@ -703,6 +705,7 @@ def run_ours(args):
 
     st = synth.workload(WORKLOAD)
     h, c, I, W, c_true = make_inputs(st, torch, tt, synth)
+    h.set_forward_kernel(args.forward_kernel)
     g = torch.empty_like(c)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     for _ in range(max(args.warmup, 3)):
@@ -817,6 +820,7 @@ def run_ours(args):
                 "unweighted": {"value": e2e_nw, "h2d_bytes_per_step": h2d - W.numel() * 4,
                                "note": "W = 1 passed as NULL (the API's all-ones weights)"}},
         "gpu_launches": launches,
+        "forward_kernel": args.forward_kernel,
         "clocks": clocks,
         "loss": losses[-1],
     }

@@ -125,6 +125,22 @@ tt_status tt_destroy(tt_handle *h);
  * (e.g. the adjoint behind an early-returned loss) is done with the handle's
  * buffers before the new stream reuses them. */
 tt_status tt_set_stream(tt_handle *h, void *stream);
+/* Chooses the kernel of the forward projection (Eq. forward_model, the
+ * Joseph discretisation of Sec. "real_space_geom") for the calls that follow:
+ *   0  automatic (the default): the tap-pair march (1), the faster of the
+ *      two on every workload measured;
+ *   1  the tap-pair march: bilinear taps read from the L1/L2-resident volume;
+ *   2  the staged march: for each plane a copy warp moves the box of a ray
+ *      tile's taps into shared memory with one tensor copy, and the rays read
+ *      them there.  Applies to TT_F32 handles with 16 padded channels
+ *      (ell_max 4) whose boxes fit the shared-memory ring (at most 32 voxels
+ *      wide); TT_UNSUPPORTED otherwise.
+ * Both compute the same FP32 ray sums (the same products added in the same
+ * order), so projections and residual contractions agree bit for bit; the
+ * loss is summed over ray tiles of different shapes and may differ in the
+ * last bits.  Call it between evaluations on the handle's stream (it changes
+ * only host state).  Other values: TT_INVALID_ARG. */
+tt_status tt_set_forward_kernel(tt_handle *h, int kind);
 /* Shape query: any out-pointer may be NULL. */
 tt_status tt_get_sizes(const tt_handle *h, int *K, int *K_padded, long long *n_vox, long long *n_data);
 

@@ -8,6 +8,8 @@
 #include <string>
 #include <type_traits>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -404,7 +406,7 @@ tt_status validate(const tt_problem *P)
 static void free_handle(tt_handle *h)
 {
     if (!h) return;
-    cudaFree(h->geo); cudaFree(h->B64); cudaFree(h->Bp); cudaFree(h->cpad); cudaFree(h->gpad);
+    cudaFree(h->geo); cudaFree(h->tmaps); cudaFree(h->B64); cudaFree(h->Bp); cudaFree(h->cpad); cudaFree(h->gpad);
     cudaFree(h->G); cudaFree(h->partials); cudaFree(h->loss_dev); cudaFree(h->red);
     cudaFree(h->hc); cudaFree(h->hI); cudaFree(h->hW); cudaFree(h->hg);
     for (cudaEvent_t e : h->chunk_ready) cudaEventDestroy(e);
@@ -422,10 +424,97 @@ static void free_handle(tt_handle *h)
     delete h;
 }
 
-static long long forward_ctas(const tt_handle *h)
+static long long forward_ctas(const tt_handle *h, bool staged)
 {
-    const int TK = fwd_tk(h->LG), TJ = fwd_tj(h->LG);
+    const int TK = staged ? kStTK : fwd_tk(h->LG), TJ = staged ? kStTJ : fwd_tj(h->LG);
     return (long long)((h->nk + TK - 1) / TK) * ((h->nj + TJ - 1) / TJ) * h->S;
+}
+
+// Box of the staged forward for projection g: a tile's rays span W = (TJ - 1)
+// |uj| + (TK - 1)|uk| in u at every plane (the rays are parallel), and the
+// rows floor(c) and floor(c) + 1 for c within kStEps of that span number at
+// most floor(W + 2 kStEps) + 3; likewise in v.  1e-3 voxels more covers the
+// FP32 rounding of the ray coordinates.
+static void stage_box(const ProjGeom &g, int nj, int nk, int &ru, int &rv)
+{
+    const double tj = std::min(kStTJ, nj) - 1, tk = std::min(kStTK, nk) - 1;
+    const double m = 2.0 * kStEps + 1e-3;
+    ru = (int)std::floor(tj * std::fabs(g.uj) + tk * std::fabs(g.uk) + m) + 3;
+    rv = (int)std::floor(tj * std::fabs(g.vj) + tk * std::fabs(g.vk) + m) + 3;
+}
+
+// The driver's tensor-map encoder, looked up once through the runtime.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        (void)cudaGetLastError();
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// Tensor map of projection g's plane box over the padded volume copy it
+// reads.  The copy is viewed as a 3-D tensor of 8-byte words: the innermost
+// dimension merges v and the 16 channels (8 words per voxel), then the middle
+// axis (y) and the outer axis (x for the z-innermost copy, z for the other).
+// The box is st_rv voxels wide and st_ru rows long along u (the middle or the
+// outer axis), one plane thick along the main axis; coordinates outside the
+// tensor read as zero.
+static bool encode_box_map(const tt_handle *h, const ProjGeom &g, TmaDesc *out)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const int nin = g.copy ? h->N[0] : h->N[2], nout = g.copy ? h->N[2] : h->N[0];
+    const cuuint64_t dims[3] = {(cuuint64_t)8 * (nin + 4), (cuuint64_t)(h->N[1] + 4), (cuuint64_t)(nout + 4)};
+    const cuuint64_t strides[2] = {(cuuint64_t)(nin + 4) * 64, (cuuint64_t)(nin + 4) * (h->N[1] + 4) * 64};
+    const cuuint32_t box[3] = {(cuuint32_t)(8 * g.st_rv), (cuuint32_t)(g.st_umid ? g.st_ru : 1),
+                               (cuuint32_t)(g.st_umid ? 1 : g.st_ru)};
+    const cuuint32_t elem[3] = {1, 1, 1};
+    void *base = (char *)h->cpad + (g.copy ? h->pad_vox * 64 : 0);
+    static_assert(sizeof(TmaDesc) == sizeof(CUtensorMap), "tensor-map size");
+    CUtensorMap m;
+    const CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, base, dims, strides, box, elem,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    std::memcpy(out, &m, sizeof(m));
+    return true;
+}
+
+// The staged forward applies to FP32 storage with 16 padded channels when
+// kStRing boxes of the largest size fit in the shared memory of one CTA, every
+// box is at most kStMaxRv voxels wide, and the driver encodes the tensor maps.
+// Sets each projection's box, the ring size and the maps (enqueued on the
+// handle's stream).
+static void plan_forward(tt_handle *h)
+{
+    h->stage_cap = 0;
+    if (h->prec != TT_F32 || h->KP != 16) return;
+    long long cap = 0;
+    bool fits = true;
+    for (ProjGeom &g : h->geo_host) {
+        stage_box(g, h->nj, h->nk, g.st_ru, g.st_rv);
+        g.st_umid = g.u == 1 ? 1 : 0;
+        fits = fits && g.st_rv <= kStMaxRv && g.st_ru <= 256;
+        cap = std::max(cap, (long long)((g.st_ru * g.st_rv + 1) & ~1));
+    }
+    const long long bytes = (long long)kStRing * cap * 16 * 4 + (long long)h->CP * 16 * 4 + 128;
+    if (!fits || bytes > kStMaxSmem) return;
+    h->tmaps_host.resize(h->S);
+    for (int s = 0; s < h->S; ++s)
+        if (!encode_box_map(h, h->geo_host[s], &h->tmaps_host[s])) return;
+    if (cudaMalloc((void **)&h->tmaps, sizeof(TmaDesc) * h->S) != cudaSuccess ||
+        cudaMemcpyAsync(h->tmaps, h->tmaps_host.data(), sizeof(TmaDesc) * h->S, cudaMemcpyHostToDevice, h->stream) !=
+            cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    h->stage_cap = (int)cap;
 }
 
 // Checks a device pointer argument: non-null, 16-byte aligned.
@@ -661,8 +750,10 @@ tt_status tt_create(const tt_problem *P, tt_precision prec, void *stream, tt_han
     }
     ALLOC(h->gpad, es * h->nvox() * h->KP);
     ALLOC(h->G, es * h->npix() * h->KP);
-    h->n_fwd_ctas = forward_ctas(h);
-    h->n_partials = h->n_fwd_ctas;
+    plan_forward(h);
+    h->fwd_staged = false;   // the tap-pair march is the faster one on every measured workload
+    h->n_fwd_ctas = forward_ctas(h, h->fwd_staged);
+    h->n_partials = std::max(forward_ctas(h, false), forward_ctas(h, true));
     ALLOC(h->partials, sizeof(double) * h->n_partials);
     ALLOC(h->loss_dev, sizeof(double) * 4);
     ALLOC(h->red, sizeof(double) * dot_blocks(h));
@@ -724,6 +815,20 @@ tt_status tt_set_stream(tt_handle *h, void *stream)
     TT_CUDA(cudaEventRecord(h->stream_switch, h->stream), "tt_set_stream: event record");
     TT_CUDA(cudaStreamWaitEvent(next, h->stream_switch, 0), "tt_set_stream: stream wait");
     h->stream = next;
+    return TT_OK;
+}
+
+tt_status tt_set_forward_kernel(tt_handle *h, int kind)
+{
+    if (!h) return invalid("null handle");
+    if (kind < kFwdAuto || kind > kFwdStaged) return invalid("tt_set_forward_kernel: kind must be 0, 1 or 2");
+    if (kind == kFwdStaged && h->stage_cap == 0) {
+        set_error("tt_set_forward_kernel: the staged forward needs FP32 storage, 16 padded channels and a stage ring "
+                  "that fits in shared memory");
+        return TT_UNSUPPORTED;
+    }
+    h->fwd_staged = kind == kFwdStaged;
+    h->n_fwd_ctas = forward_ctas(h, h->fwd_staged);
     return TT_OK;
 }
 

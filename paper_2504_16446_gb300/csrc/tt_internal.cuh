@@ -27,6 +27,27 @@ __host__ __device__ constexpr int fwd_rays(int LG) { return kFwdThreads / LG; }
 __host__ __device__ constexpr int fwd_tk(int LG) { return fwd_rays(LG) >= 256 ? 16 : 8; }
 __host__ __device__ constexpr int fwd_tj(int LG) { return fwd_rays(LG) / fwd_tk(LG); }
 
+// Staged forward march (FP32 storage, 16 padded channels): a CTA of eight
+// consumer warps and one copy warp marches a tile of kStTJ x kStTK rays with
+// its taps read from a ring of shared-memory stages, one plane's box of
+// padded-volume voxels per stage, moved by one tensor copy.  The ring holds
+// kStRing boxes of the largest size over the projections; a projection with
+// smaller boxes runs as many stages as fit, up to kStMaxDepth.  kStEps
+// (voxels) widens the box against the rounding of the ray coordinates.
+constexpr int kStTJ = 8, kStTK = 16, kStRing = 3, kStMaxDepth = 8;
+constexpr int kStConsumers = 256, kStThreads = kStConsumers + 32;
+constexpr float kStEps = 1.0f / 64;
+constexpr long long kStMaxSmem = 200 * 1024;   // dynamic shared memory the ring may take (one CTA per SM)
+constexpr int kStMaxRv = 32;                   // box width along v: 8 x 16 B words per voxel, at most 256 words
+
+// An opaque tensor-map object (the driver's 128-byte, 64-byte aligned
+// descriptor of a tiled tensor copy), kept in device memory per projection.
+struct alignas(64) TmaDesc {
+    unsigned char bytes[128];
+};
+// Forward kernels a handle can run (tt_set_forward_kernel).
+enum { kFwdAuto = 0, kFwdL1 = 1, kFwdStaged = 2 };
+
 // Lane-group width (lanes that share one ray or one voxel, each holding
 // KP/LG channels) and padded channel count for a band limit.
 __host__ __device__ constexpr int lane_group(int K) { return K <= 4 ? 1 : (K <= 8 ? 2 : 4); }
@@ -67,6 +88,10 @@ struct ProjGeom {
     int Nm, Nu, Nv;
     int sm, su, sv;           // strides of the axes in the padded volume copy the projection reads
     int copy;                 // 0: cpad (z innermost), 1: the x-innermost copy; sv == 1 in both
+    // Staged forward: the box of one plane is st_ru rows (along u) of st_rv
+    // voxels (along v); st_umid: u is the middle axis (y) of the volume copy,
+    // else its outer axis.
+    int st_ru, st_rv, st_umid;
 };
 
 // Per-projection constants of the adjoint gather in the element type.  The
@@ -153,6 +178,13 @@ struct tt_handle {
     double *partials = nullptr;          // device, per-CTA loss partials
     long long n_partials = 0;            // allocated entries
     long long n_fwd_ctas = 0;            // entries the forward kernel writes
+    // Staged forward march: voxels of the largest plane box over the
+    // projections, rounded up to even (0 when the kernel does not apply),
+    // and whether the forward runs it.
+    int stage_cap = 0;
+    bool fwd_staged = false;
+    tt::TmaDesc *tmaps = nullptr;        // device [S]: tensor map of each projection's plane box
+    std::vector<tt::TmaDesc> tmaps_host;
     double *red = nullptr;               // device, dot_blocks(h) partials of the regulariser reductions
     double *loss_dev = nullptr;          // device scalars: [0] loss, [1] regulariser value
     double *loss_pinned = nullptr;       // pinned host scalar
@@ -326,5 +358,11 @@ cudaError_t vec_sub(tt_handle *h, T *out, const T *x, const T *y, long long n);
 int current_sm_count();
 // CTAs of the dot-product and regulariser reductions: four per SM.
 inline int dot_blocks(const tt_handle *h) { return 4 * h->n_sm; }
+// Dynamic shared memory of the staged forward: the stage ring, B_s and 128
+// bytes of slack to align the ring.
+inline size_t staged_forward_smem(const tt_handle *h)
+{
+    return (size_t)kStRing * h->stage_cap * 16 * sizeof(float) + (size_t)h->CP * 16 * sizeof(float) + 128;
+}
 
 }  // namespace tt

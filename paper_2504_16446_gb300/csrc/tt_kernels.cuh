@@ -16,10 +16,12 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <climits>
 #include <type_traits>
 #include <vector>
 
 #include "tt_internal.cuh"
+#include "tt_umma.cuh"
 
 namespace tt {
 
@@ -250,6 +252,16 @@ __device__ __forceinline__ double sum_fixed_order(const double *__restrict__ p, 
     return block_sum(v, red);
 }
 
+// Transverse coordinates of ray (j, k) on plane 0, u0 + j uj + k uk and
+// v0 + j vj + k vk, in FP64 with explicit FMAs (one rounding order for every
+// kernel that marches rays), rounded once to T.
+template <typename T>
+__device__ __forceinline__ void ray_base(const ProjGeom &P, int j, int k, T &ur, T &vr)
+{
+    ur = (T)__fma_rn((double)k, P.uk, __fma_rn((double)j, P.uj, P.u0));
+    vr = (T)__fma_rn((double)k, P.vk, __fma_rn((double)j, P.vj, P.v0));
+}
+
 // Range of planes p in [0, Nm-1] on which coordinate w(p) = w0 + p*dw lies
 // in (-1, N), i.e. can give a bilinear tap inside [0, N-1].  floor/ceil of the
 // bounds may add one plane on each side; those planes see only the zero
@@ -402,9 +414,9 @@ k_forward(const ProjGeom *__restrict__ geo, const S *__restrict__ cpad /* interi
 
     const ProjGeom &P = geo[s];
     // Ray base in FP64 (one rounding to T), per-plane stepping in T.
-    const double urd = P.u0 + (double)j * P.uj + (double)k * P.uk;
-    const double vrd = P.v0 + (double)j * P.vj + (double)k * P.vk;
-    const T ur = (T)urd, vr = (T)vrd, up = (T)P.up, vp = (T)P.vp;
+    T ur, vr;
+    ray_base<T>(P, j, k, ur, vr);
+    const T up = (T)P.up, vp = (T)P.vp;
     const int Nu = P.Nu, Nv = P.Nv, sm = P.sm, su = P.su;
     T lo = T(0), hi = T(P.Nm - 1);
     clip_planes<T>(ur, up, Nu, lo, hi);
@@ -501,6 +513,243 @@ k_forward(const ProjGeom *__restrict__ geo, const S *__restrict__ cpad /* interi
             tot = block_sum((q == 0 && valid) ? (double)lossr : 0.0, red);
         // canonical CTA index (projection, j tile, k tile): the same for
         // either CTA order and for chunked launches, so the loss sums alike
+        if (threadIdx.x == 0) partials[((long long)s * tiles_j + tj) * tiles_k + tk] = tot;
+    }
+}
+
+// --------------------------------------------- staged forward (FP32, KP = 16)
+//
+// The ray sums of k_forward with the bilinear taps read from shared memory.
+// One CTA = one projection x a tile of kStTJ x kStTK rays.  Warp 8 (the copy
+// warp) walks the tile's planes and, for each, copies the box of the padded
+// volume copy that holds the tile's taps -- st_ru rows along u of st_rv
+// voxels along v, one plane thick -- into the next stage of a ring with one
+// tiled tensor copy, completing on the stage's `full` mbarrier; a stage is
+// refilled once all eight consumer warps have arrived on its `empty`
+// mbarrier.  Parallel rays shift rigidly from plane to plane, so the box of an
+// 8 x 16 tile holds about half as many voxels as the tile reads taps, and
+// every read hits shared memory.  The ring has room for kStRing boxes of the
+// largest size over the projections; a projection whose boxes are smaller
+// runs min(kStMaxDepth, room / box) stages, so more planes are in flight.
+// (One tensor copy per plane: bulk copies of the box's rows one by one were
+// measured to cost a request each, three times the time of the bytes.)
+//
+// Consumers: four lanes per ray and two rays per lane group (j and j + 4).
+// Lane q owns the eight floats [8q, 8q + 8) of each tap pair, exactly as in
+// k_forward, read as two 16-byte chunks 2q and 2q + 1; lanes of odd groups
+// read them in the order (2q + 1, 2q).  A quarter-warp (two groups) then
+// reads, per instruction, the even chunks of one pair and the odd chunks of
+// the other, whose 16-byte bank groups differ for any two pairs that start on
+// 64-byte boundaries: no bank conflicts.  Per plane each ray adds the pair of
+// row iu, then that of row iu + 1, with k_forward's weights in k_forward's
+// order, so both kernels give the same FP32 sums bit for bit.
+//
+// A wait that gives up (a bounded number of polls) makes the tile's rays
+// NaN, which the loss and every output show; the copy warp waits (bounded)
+// for its copies in flight before the CTA exits.
+struct StageHdr {
+    int ulo, vlo;
+};
+constexpr uint32_t kStWaitTries = 1u << 22;
+
+// First row of a box of n rows that holds floor(c) and floor(c) + 1 for every
+// coordinate c in [cmin, cmax], the start clamped to [-2, N] (where the
+// clamped tap indices of k_forward lie).
+__device__ __forceinline__ int stage_lo(float cmin, int N)
+{
+    return min(max((int)floorf(cmin - kStEps), -2), N);
+}
+
+template <bool GRAD>
+__global__ void __launch_bounds__(kStThreads, 2)
+k_forward_staged(const ProjGeom *__restrict__ geo, const TmaDesc *__restrict__ tmaps, const float *__restrict__ Bp,
+                 int nj, int nk, int C, int CP, int tiles_k, int slab_order, int s_base, int cap,
+                 float *__restrict__ Iout, const float *__restrict__ Id, const float *__restrict__ Wd,
+                 float *__restrict__ G, double *__restrict__ partials)
+{
+    constexpr int KP = 16, LG = 4, CPL = 4, NR = 2;
+    // The tensor copies write 128-byte aligned stages: the dynamic shared
+    // memory holds 128 bytes of slack and the ring starts at its first
+    // 128-byte boundary.
+    extern __shared__ __align__(1024) unsigned char st_smem[];
+    unsigned char *ring = st_smem + ((128u - (umma::smem_u32(st_smem) & 127u)) & 127u);
+    float *stages = reinterpret_cast<float *>(ring);           // kStRing * cap voxels of KP floats
+    float *Bs = stages + (size_t)kStRing * cap * KP;           // [CP][KP]
+    __shared__ __align__(8) uint64_t full[kStMaxDepth], empty[kStMaxDepth];
+    __shared__ StageHdr hdr[kStMaxDepth];
+    __shared__ int prange[2];
+    __shared__ Dot2 red[kStThreads / 32];
+
+    int tk, s, tj, tiles_j;
+    if (slab_order) { tk = blockIdx.x % tiles_k; s = s_base + blockIdx.x / tiles_k; tj = blockIdx.y; tiles_j = gridDim.y; }
+    else { s = s_base + blockIdx.y; tj = blockIdx.x / tiles_k; tk = blockIdx.x % tiles_k; tiles_j = gridDim.x / tiles_k; }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool copier = warp == kStConsumers / 32;
+
+    const float *Bsrc = Bp + (size_t)s * CP * KP;
+    for (int t = threadIdx.x; t < CP * KP; t += kStThreads) Bs[t] = Bsrc[t];
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kStMaxDepth; ++i) {
+            umma::mbar_init(&full[i], 1);
+            umma::mbar_init(&empty[i], kStConsumers / 32);
+        }
+        prange[0] = INT_MAX;
+        prange[1] = INT_MIN;
+    }
+    __syncthreads();
+
+    const ProjGeom &P = geo[s];
+    const float up = (float)P.up, vp = (float)P.vp;
+    const int Nu = P.Nu, Nv = P.Nv;
+
+    // consumer rays: group g, lane q; rays (j0 + 4 r, k)
+    const int g = threadIdx.x / LG, q = threadIdx.x % LG;
+    const int k = tk * kStTK + g % kStTK, j0 = tj * kStTJ + g / kStTK;
+    float ur[NR], vr[NR];
+    int plo[NR], phi[NR];
+    bool valid[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int j = j0 + 4 * r;
+        valid[r] = !copier && j < nj && k < nk;
+        ray_base<float>(P, j, k, ur[r], vr[r]);
+        float lo = 0.f, hi = (float)(P.Nm - 1);
+        clip_planes<float>(ur[r], up, Nu, lo, hi);
+        clip_planes<float>(vr[r], vp, Nv, lo, hi);
+        plo[r] = valid[r] ? max(0, (int)floorf(lo)) : 1;
+        phi[r] = valid[r] ? min(P.Nm - 1, (int)ceilf(hi)) : 0;
+        if (q == 0 && plo[r] <= phi[r]) {
+            atomicMin(&prange[0], plo[r]);
+            atomicMax(&prange[1], phi[r]);
+        }
+    }
+    __syncthreads();
+    const int p0 = prange[0], np = prange[1] >= prange[0] ? prange[1] - prange[0] + 1 : 0;
+
+    float acc[NR][8];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[r][i] = 0.f;
+    bool ok = true;
+
+    // This projection's ring: stages of ru x rv voxels, rounded up to an even
+    // count so that every stage starts on a 128-byte boundary.
+    const int ru = P.st_ru, rv = P.st_rv;
+    const int sstride = (ru * rv + 1) & ~1;
+    const int depth = min(kStMaxDepth, (kStRing * cap) / sstride);
+
+    if (copier) {
+        // Lower tile extents at plane 0 from its corner rays (the coordinates
+        // are affine in j, k; the corners are those of the rays inside the
+        // detector), computed like each ray's.
+        const int jc = min(tj * kStTJ + ((lane & 1) ? kStTJ - 1 : 0), nj - 1);
+        const int kc = min(tk * kStTK + ((lane & 2) ? kStTK - 1 : 0), nk - 1);
+        float umin, vmin;
+        ray_base<float>(P, jc, kc, umin, vmin);
+#pragma unroll
+        for (int off = 1; off <= 2; off <<= 1) {
+            umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, off));
+            vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, off));
+        }
+        if (lane == 0) {   // one thread issues every copy of the tile
+            const TmaDesc *tm = tmaps + s;
+            umma::tensormap_acquire(tm);
+            int st = 0, ph = 0, issued = 0;
+            for (int n = 0; n < np; ++n) {
+                if (n >= depth && !umma::mbar_wait(&empty[st], ph ^ 1, kStWaitTries)) break;
+                const float pf = (float)(p0 + n);
+                const int ulo = stage_lo(fmaf(pf, up, umin), Nu), vlo = stage_lo(fmaf(pf, vp, vmin), Nv);
+                hdr[st] = StageHdr{ulo, vlo};
+                umma::mbar_arrive_expect_tx(&full[st], (uint32_t)(ru * rv * KP * 4));
+                // tensor coordinates of the padded copy: voxel index + 2, 8 words per voxel
+                const int pc = p0 + n + 2, uc = ulo + 2;
+                umma::tma_load_3d(stages + (size_t)st * sstride * KP, tm, 8 * (vlo + 2), P.st_umid ? uc : pc,
+                                  P.st_umid ? pc : uc, &full[st]);
+                issued = n + 1;
+                if (++st == depth) { st = 0; ph ^= 1; }
+            }
+            // no copy may still be writing shared memory when the CTA exits
+            for (int n = max(0, issued - depth); n < issued; ++n)
+                umma::mbar_wait(&full[n % depth], (n / depth) & 1, kStWaitTries);
+        }
+        __syncwarp();
+    } else {
+        const int pi = g & 1;
+        const int c0 = 2 * q + pi, c1 = 2 * q + 1 - pi;   // 16-byte chunks of a pair, in read order
+        const int h = q >> 1;                             // voxel iv + h of the pair holds lane q's channels
+        const int lim = ru * rv - rv - 2;                 // keeps both pairs of a tap inside the box
+        int st = 0, ph = 0;
+        for (int n = 0; n < np; ++n) {
+            // every lane observes the stage's completion; the warp gives up as one
+            if (!__all_sync(0xffffffffu, umma::mbar_wait(&full[st], ph, kStWaitTries))) { ok = false; break; }
+            const StageHdr hd = hdr[st];
+            const float *sb = stages + (size_t)st * sstride * KP;
+            const int p = p0 + n;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                if (p < plo[r] || p > phi[r]) continue;
+                const float u = fmaf((float)p, up, ur[r]), v = fmaf((float)p, vp, vr[r]);
+                const float fu = floorf(u), fv = floorf(v);
+                const int iu = min(max((int)fu, -2), Nu), iv = min(max((int)fv, -2), Nv);
+                const float wu = u - fu, wv = v - fv;
+                const int idx = min(max((iu - hd.ulo) * rv + (iv - hd.vlo), 0), lim);
+                const float *t0 = sb + (size_t)idx * KP;
+                const float *t1 = t0 + (size_t)rv * KP;
+                const float4 a0 = *reinterpret_cast<const float4 *>(t0 + 4 * c0);
+                const float4 a1 = *reinterpret_cast<const float4 *>(t0 + 4 * c1);
+                const float4 b0 = *reinterpret_cast<const float4 *>(t1 + 4 * c0);
+                const float4 b1 = *reinterpret_cast<const float4 *>(t1 + 4 * c1);
+                const float wvh = h ? wv : 1.f - wv;
+                const float w0 = (1.f - wu) * wvh, w1 = wu * wvh;
+                float *A = acc[r];
+                fma2(A[0], A[1], w0, a0.x, a0.y);
+                fma2(A[2], A[3], w0, a0.z, a0.w);
+                fma2(A[4], A[5], w0, a1.x, a1.y);
+                fma2(A[6], A[7], w0, a1.z, a1.w);
+                fma2(A[0], A[1], w1, b0.x, b0.y);
+                fma2(A[2], A[3], w1, b0.z, b0.w);
+                fma2(A[4], A[5], w1, b1.x, b1.y);
+                fma2(A[6], A[7], w1, b1.z, b1.w);
+            }
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&empty[st]);
+            if (++st == depth) { st = 0; ph ^= 1; }
+        }
+        if (pi) {   // chunk order back to (2q, 2q + 1)
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float t = acc[r][i];
+                    acc[r][i] = acc[r][4 + i];
+                    acc[r][4 + i] = t;
+                }
+        }
+    }
+    __syncthreads();
+
+    Dot2 lossr{0.f, 0.f};
+    if (!copier) {
+        const float step = (float)P.step;
+        const int chunk = (q % 2) * 2 + (q >> 1);
+        const float bad = __int_as_float(0x7fc00000);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            // both voxels' sums in every lane of a pair; lane q keeps chunk `chunk`
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[r][i] += __shfl_xor_sync(0xffffffffu, acc[r][i], LG / 2);
+            float accq[CPL];
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) accq[i] = ok ? ((q >> 1) ? acc[r][CPL + i] : acc[r][i]) * step : bad;
+            const long long pix = ((long long)s * nj + (j0 + 4 * r)) * nk + k;
+            const float lr = forward_epilogue<float, float, CPL, KP, LG, GRAD>(accq, q, chunk, valid[r], true, pix, Bs,
+                                                                           C, CP, Iout, Id, Wd, G);
+            if (q == 0 && valid[r]) dot2_add1(lossr, lr);
+        }
+    }
+    if constexpr (GRAD) {
+        const double tot = dot2_block_sum(lossr, red);
         if (threadIdx.x == 0) partials[((long long)s * tiles_j + tj) * tiles_k + tk] = tot;
     }
 }
@@ -841,17 +1090,41 @@ cudaError_t launch_forward_L(tt_handle *h, T *Iout, const T *I, const T *W, bool
     if (s1 < 0) s1 = h->S;
     const int ns = s1 - s0;
     constexpr int K = num_coeffs(L), KP = padded_k(K), LG = lane_group(K);
-    constexpr int TK = fwd_tk(LG), TJ = fwd_tj(LG);
-    const int tiles_k = (h->nk + TK - 1) / TK, tiles_j = (h->nj + TJ - 1) / TJ;
     // slab order once the padded volume would take more than half of L2
     const long long vol_bytes = (long long)(h->N[0] + 4) * (h->N[1] + 4) * (h->N[2] + 4) * KP * sizeof(S);
     const int slab = vol_bytes > (64LL << 20) ? 1 : 0;
-    const dim3 grid = slab ? dim3(tiles_k * ns, tiles_j) : dim3(tiles_k * tiles_j, ns);
-    const size_t smem = (size_t)h->CP * KP * sizeof(T);
     const T *Bp = (const T *)h->Bp;
     const S *cpad = (const S *)h->cpad + h->cpad_origin * KP;
     const S *cpadx = h->xcopy ? (const S *)h->cpad + (h->pad_vox + h->cpadx_origin) * KP : nullptr;
     cudaEvent_t ev;
+    if constexpr (std::is_same<T, float>::value && std::is_same<S, float>::value && KP == 16) {
+        if (h->fwd_staged) {
+            const int tiles_k = (h->nk + kStTK - 1) / kStTK, tiles_j = (h->nj + kStTJ - 1) / kStTJ;
+            const dim3 grid = slab ? dim3(tiles_k * ns, tiles_j) : dim3(tiles_k * tiles_j, ns);
+            const size_t smem = staged_forward_smem(h);
+            prof_begin(h, TT_KSLOT_FORWARD, &ev);
+            if (grad) {
+                auto kern = k_forward_staged<true>;
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                kern<<<grid, kStThreads, smem, h->stream>>>(h->geo, h->tmaps, Bp, h->nj, h->nk, h->C, h->CP, tiles_k,
+                                                            slab, s0, h->stage_cap, nullptr, I, W, (T *)h->G,
+                                                            h->partials);
+            } else {
+                auto kern = k_forward_staged<false>;
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                kern<<<grid, kStThreads, smem, h->stream>>>(h->geo, h->tmaps, Bp, h->nj, h->nk, h->C, h->CP, tiles_k,
+                                                            slab, s0, h->stage_cap, Iout, nullptr, nullptr, nullptr,
+                                                            nullptr);
+            }
+            cudaError_t e = cudaGetLastError();
+            prof_end(h, TT_KSLOT_FORWARD, ev);
+            return e;
+        }
+    }
+    constexpr int TK = fwd_tk(LG), TJ = fwd_tj(LG);
+    const int tiles_k = (h->nk + TK - 1) / TK, tiles_j = (h->nj + TJ - 1) / TJ;
+    const dim3 grid = slab ? dim3(tiles_k * ns, tiles_j) : dim3(tiles_k * tiles_j, ns);
+    const size_t smem = (size_t)h->CP * KP * sizeof(T);
     prof_begin(h, TT_KSLOT_FORWARD, &ev);
     if (grad) {
         auto kern = k_forward<T, S, KP, LG, true>;

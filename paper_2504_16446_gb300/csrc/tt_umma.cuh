@@ -104,6 +104,50 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint3
     return false;
 }
 
+// Arrive on the mbarrier (count one), and the same with `bytes` more
+// transaction bytes expected in the current phase.
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bulk asynchronous copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) from global to this CTA's shared memory, completing as
+// transaction bytes on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+                 : "memory");
+}
+
+// Tiled tensor copy of one box from global to this CTA's shared memory (dst
+// 128-byte aligned), described by the tensor map at tmap (device global
+// memory) at coordinates (c0, c1, c2), innermost first; the box's bytes
+// complete as transaction bytes on the mbarrier.  c0 times the element size
+// must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int c0, int c1, int c2, uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(mbar))
+        : "memory");
+}
+
+// Makes a tensor map written to global memory by ordinary stores visible to
+// the tensor-copy unit (once per CTA before its first copy).
+__device__ __forceinline__ void tensormap_acquire(const void *tmap)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
+}
+
 // 16 consecutive 32-bit columns of this warp's 32 tensor-memory lanes, one
 // lane per thread (shape 32x32b).  taddr: lane in bits 31-16, column in 15-0.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])

@@ -66,6 +66,7 @@ SIGNATURES = {
     "tt_create": (ctypes.c_int, [ctypes.POINTER(_Problem), ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "tt_destroy": (ctypes.c_int, [_P]),
     "tt_set_stream": (ctypes.c_int, [_P, _P]),
+    "tt_set_forward_kernel": (ctypes.c_int, [_P, ctypes.c_int]),
     "tt_get_sizes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "tt_basis_matrix": (ctypes.c_int, [_P, _P]),
@@ -220,6 +221,13 @@ class Handle:
 
     def _sync_stream(self):
         _check(self.lib.tt_set_stream(self._h, _stream_ptr()), "tt_set_stream")
+
+    FORWARD_KERNELS = {"auto": 0, "l1": 1, "staged": 2}
+
+    def set_forward_kernel(self, kind: str) -> None:
+        """Forward-projection kernel for the calls that follow: "auto", "l1" (taps read
+        from the L1/L2-resident volume) or "staged" (taps staged in shared memory)."""
+        _check(self.lib.tt_set_forward_kernel(self._h, self.FORWARD_KERNELS[kind]), "tt_set_forward_kernel")
 
     @property
     def _sfx(self):
