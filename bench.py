@@ -470,8 +470,10 @@ def noise_free_residual(h, c_true, torch, tt, target: float = 1e-3, max_iter: in
 
 def measure_forms(torch, tt, synth, flush, steps: int = 20):
     """ms per gradient evaluation of the FP32, bfloat16- and float16-storage
-    forms on the 64^3 (l_max 4) and 128^3 (l_max 8, 240 x 128^2 x 8) workloads;
-    random O(1) volume and data, L2 flushed between evaluations."""
+    forms on the 64^3 (l_max 4) and 128^3 (l_max 8, 240 x 128^2 x 8) workloads,
+    and at l_max 4 the FP32 form with the staged forward march
+    (tt_set_forward_kernel 2) as "f32_staged"; random O(1) volume and data, L2
+    flushed between evaluations."""
     res = {}
     for wl in ("ell64", "ell128"):
         st = synth.workload(wl)
@@ -481,8 +483,12 @@ def measure_forms(torch, tt, synth, flush, steps: int = 20):
         I = torch.rand(st.data_shape, device="cuda", generator=gen) * st.shape[0]
         g = torch.empty_like(c)
         row = {}
-        for prec in ("f32", "bf16", "f16"):
-            h = tt.Handle(st, prec)
+        for prec in ("f32", "f32_staged", "bf16", "f16"):
+            if prec == "f32_staged" and st.ell_max != 4:
+                continue
+            h = tt.Handle(st, "f32" if prec == "f32_staged" else prec)
+            if prec == "f32_staged":
+                h.set_forward_kernel("staged")
             for _ in range(3):
                 h.gradient_residual(c, I, None, out=g)
             h.profile(True)
