@@ -443,17 +443,16 @@ static void stage_box(const ProjGeom &g, int nj, int nk, int &ru, int &rv)
     rv = (int)std::floor(tj * std::fabs(g.vj) + tk * std::fabs(g.vk) + m) + 3;
 }
 
-// The driver's tensor-map encoder, looked up once through the runtime.
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+void *driver_tensor_map_encoder()
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    static void *fn = [] {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
             q != cudaDriverEntryPointSuccess)
             p = nullptr;
         (void)cudaGetLastError();
-        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        return p;
     }();
     return fn;
 }
@@ -467,7 +466,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 // tensor read as zero.
 static bool encode_box_map(const tt_handle *h, const ProjGeom &g, TmaDesc *out)
 {
-    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    const auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(driver_tensor_map_encoder());
     if (!enc) return false;
     const int nin = g.copy ? h->N[0] : h->N[2], nout = g.copy ? h->N[2] : h->N[0];
     const cuuint64_t dims[3] = {(cuuint64_t)8 * (nin + 4), (cuuint64_t)(h->N[1] + 4), (cuuint64_t)(nout + 4)};

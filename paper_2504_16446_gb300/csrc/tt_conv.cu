@@ -8,7 +8,9 @@
 // (channels zero padded); convolution weights wk[t][Cout][Cin] bfloat16, t =
 // (dx+1)*9 + (dy+1)*3 + (dz+1); "same" zero padding, cross-correlation:
 //   y[v][co] = sum_t sum_ci a[v + d_t][ci] * wk[t][co][ci].
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -68,15 +70,22 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
 // per CTA as [dx,dy][CIN/8][dz * COUT + co][8] (SBO = 128 B, LBO = 3 COUT
 // 16 B).
 //
-// Pipeline.  A persistent CTA walks runs of seg_len consecutive x planes of one
-// (y, z) tile column.  Tile x needs planes x-1, x, x+1 from a ring of four
-// plane buffers, so each step stages one new plane.  Step for tile x: one
-// thread issues its MMAs into tensor-memory accumulator x % 2 and commits
-// them to mbarrier x % 2; while they run, all eight warps issue the global
-// loads of plane x+3 into registers, wait for tile x-1's mbarrier, write tile
-// x-1 out (ReLU, bf16 or f32), and store plane x+2 -- loaded a step earlier
-// -- into the buffer that tile x-1 was the last to read.  A wait that gives
-// up writes NaN into its tile, which every consumer of the output sees.
+// Pipeline.  A persistent CTA walks runs of consecutive x planes of one (y, z)
+// tile column.  Tile x needs planes x-1, x, x+1 from a ring of NBUF plane
+// buffers (4 for 32 -> 32 channels, more where the weights are smaller), so
+// each step stages one new plane, NBUF - 3 steps ahead.  A plane is one tiled tensor
+// copy: the input viewed as a 5-D tensor (8 channels, z, y, channel group,
+// x) whose box of 8 x 32 x 6 x CIN/8 x 1 elements lands in exactly the
+// buffer layout above, zeros outside the volume; it completes on the
+// buffer's own mbarrier.  Step for tile x: thread 0 waits for plane x+1's
+// copy, issues the tile's MMAs into tensor-memory accumulator x % 2 and
+// commits them to mbarrier x % 2; meanwhile all eight warps wait for tile
+// x-1's mbarrier, thread 0 starts the copy of plane x-2+NBUF into the buffer
+// that tile x-1 was the last to read, and all write tile x-1 out (ReLU, bf16
+// or f32).  (Staging the planes through registers by all warps was
+// measured 0.162 ms for the 32 -> 32 layer at 128^3.)  A wait that gives up
+// writes NaN into its tile, which every consumer of the output sees; at exit
+// thread 0 waits (bounded) for copies still in flight.
 constexpr uint32_t kTcWaitTries = 1u << 22;
 constexpr int kTcThreads = 256;
 constexpr int kTileZ = 30;                 // output z per tile (32 input rows)
@@ -85,63 +94,16 @@ template <int CIN, int COUT>
 struct TcConvSmem {
     static constexpr uint32_t plane = (CIN / 8) * 6 * 512;
     static constexpr uint32_t dxy = 3 * COUT * CIN * 2;       // weights of one (dx, dy): three z taps
-    static constexpr uint32_t wts = 4 * plane;
+    // plane buffers: as many as leave two CTAs per SM (110 KB each), 4..8
+    static constexpr int nbuf_fit = (int)((110u * 1024u - 9 * dxy - 256) / plane);
+    static constexpr int nbuf = nbuf_fit > 8 ? 8 : (nbuf_fit < 4 ? 4 : nbuf_fit);
+    static constexpr uint32_t wts = nbuf * plane;
+    // [0, 1] MMA commits, [2, 2 + nbuf) plane copies, then the tensor-memory
+    // slot and a failure flag
     static constexpr uint32_t mbar = wts + 9 * dxy;
-    static constexpr uint32_t bytes = mbar + 32;
+    static constexpr uint32_t bytes = mbar + 8 * (2 + nbuf) + 8;
     static constexpr uint32_t tmem_cols = 2 * 3 * COUT <= 128 ? 128 : 256;   // two accumulators of 3 COUT
 };
-
-// Stages input plane gx (zeros outside the volume) into a plane buffer:
-// chunk (kc, yh, zl) = voxel (gx, y0-1+yh, z0-1+zl), channels 8 kc .. 8 kc+7.
-// Two phases, so that the global loads can be in flight while the thread
-// waits for MMAs and writes a tile out: plane_load into registers, then
-// plane_store into the buffer.
-template <int CIN>
-struct PlaneRegs {
-    static constexpr int KC = CIN / 8, kChunks = KC * 6 * 32, kPer = (kChunks + kTcThreads - 1) / kTcThreads;
-    uint4 val[kPer];
-};
-
-template <int CIN>
-__device__ __forceinline__ void plane_load(PlaneRegs<CIN> &r, const __nv_bfloat16 *__restrict__ in, int gx, int y0,
-                                           int z0, int nx, int ny, int nz, int tid)
-{
-    using P = PlaneRegs<CIN>;
-#pragma unroll
-    for (int j = 0; j < P::kPer; ++j) {
-        const int e = tid + j * kTcThreads;
-        r.val[j] = make_uint4(0, 0, 0, 0);
-        if (e < P::kChunks) {
-            const int zl = e % 32, kc = (e / 32) % P::KC, yh = e / (32 * P::KC);
-            const int gy = y0 - 1 + yh, gz = z0 - 1 + zl;
-            if ((unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz)
-                r.val[j] = __ldg(reinterpret_cast<const uint4 *>(in + (((size_t)gx * ny + gy) * nz + gz) * CIN) + kc);
-        }
-    }
-}
-
-template <int CIN>
-__device__ __forceinline__ void plane_store(uint8_t *buf, const PlaneRegs<CIN> &r, int tid)
-{
-    using P = PlaneRegs<CIN>;
-#pragma unroll
-    for (int j = 0; j < P::kPer; ++j) {
-        const int e = tid + j * kTcThreads;
-        if (e < P::kChunks) {
-            const int zl = e % 32, kc = (e / 32) % P::KC, yh = e / (32 * P::KC);
-            *reinterpret_cast<uint4 *>(buf + (kc * 6 + yh) * 512 + zl * 16) = r.val[j];
-        }
-    }
-}
-
-template <int CIN>
-__device__ __forceinline__ void stage_plane(uint8_t *buf, const __nv_bfloat16 *__restrict__ in, int gx, int y0,
-                                            int z0, int nx, int ny, int nz, int tid)
-{
-    PlaneRegs<CIN> r;
-    plane_load<CIN>(r, in, gx, y0, z0, nx, ny, nz, tid);
-    plane_store<CIN>(buf, r, tid);
-}
 
 // Tile epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. (input rows
 // y0 + w % 4, z0 - 1 + lane) and, for its half of the output channels, the
@@ -199,19 +161,25 @@ __device__ __forceinline__ void tile_epilogue(uint32_t tmem, uint32_t acc_col, b
 
 template <int CIN, int COUT, bool RELU, bool OUT_F32>
 __global__ void __launch_bounds__(kTcThreads)
-k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ wk, void *__restrict__ out,
-                int nx, int ny, int nz, int tiles_y, int tiles_z)
+k_conv3d_fwd_tc(const __grid_constant__ CUtensorMap planes, const __nv_bfloat16 *__restrict__ wk,
+                void *__restrict__ out, int nx, int ny, int nz, int tiles_y, int tiles_z)
 {
     using L = TcConvSmem<CIN, COUT>;
     constexpr int KC = CIN / 8, NB = 3 * COUT;
     constexpr uint32_t kLboA = 6 * 512, kLboB = NB * 16;
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L::mbar);   // [2]
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L::mbar);   // [0, 1] MMA commits
+    constexpr int NBUF = L::nbuf;
+    uint64_t *pbar = mbar + 2;                                        // [NBUF] plane copies, one per buffer
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(pbar + NBUF);
+    volatile int &s_fail = *reinterpret_cast<volatile int *>(tslot + 1);   // a plane copy not seen landing
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0) umma::tmem_alloc(tslot, L::tmem_cols);
-    if (tid == 0) { umma::mbar_init(mbar, 1); umma::mbar_init(mbar + 1, 1); }
+    if (tid == 0) {
+        for (int i = 0; i < 2 + NBUF; ++i) umma::mbar_init(mbar + i, 1);
+        s_fail = 0;
+    }
     // weights [t][co][ci], t = 9 dx + 3 dy + dz  ->  [dx,dy][ci/8][dz COUT + co][8]
     for (int e = tid; e < 27 * COUT * KC; e += kTcThreads) {
         const int kc = e % KC, co = (e / KC) % COUT, t = e / (KC * COUT);
@@ -219,13 +187,18 @@ k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__res
         const uint4 v = __ldg(reinterpret_cast<const uint4 *>(wk + ((size_t)t * COUT + co) * CIN) + kc);
         *reinterpret_cast<uint4 *>(smem + L::wts + dxy * L::dxy + kc * kLboB + (dz * COUT + co) * 16) = v;
     }
+    umma::fence_async_smem();
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
     const uint32_t tmem = *tslot;
     const uint32_t idesc = umma::idesc_bf16_f32(128, NB);
     const uint32_t s_planes = umma::smem_u32(smem), s_wts = umma::smem_u32(smem + L::wts);
-    uint32_t issued[2] = {0, 0};          // tiles waited per mbarrier (parity of the next wait)
+    // Phase parities as bit masks (bit b for mbarrier b): the next wait on
+    // each MMA mbarrier; on each plane buffer (thread 0) the next wait, the
+    // count of copies started mod 2, and whether any was started.
+    uint32_t mma_par = 0, wait_par = 0, copy_par = 0, used = 0;
+    const void *pmap = &planes;
 
     // This CTA's equal share [t_begin, t_end) of the tile sequence (x fastest,
     // then the z tile, then the y tile), walked as runs of consecutive x.
@@ -237,23 +210,35 @@ k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__res
         const int y0 = ty * 4, z0 = tz * kTileZ, xa = (int)(t - col * nx);
         const int xb = (int)std::min<long long>(nx, xa + (t_end - t));
         t += xb - xa;
-        // planes xa-1, xa, xa+1 before the first tile (the ring is idle here);
-        // plane xa+2's loads go out now and are stored during the first step
-        for (int px = xa - 1; px <= xa + 1; ++px)
-            stage_plane<CIN>(smem + (px & 3) * L::plane, in, px, y0, z0, nx, ny, nz, tid);
-        PlaneRegs<CIN> next;
-        if (xa + 2 <= xb) plane_load<CIN>(next, in, xa + 2, y0, z0, nx, ny, nz, tid);
+        // thread 0 starts and awaits the copies; plane px (>= -1) goes to
+        // buffer (px + NBUF) % NBUF
+        auto copy_plane = [&](int px) {
+            const int bf = (px + NBUF) % NBUF;
+            umma::mbar_arrive_expect_tx(pbar + bf, L::plane);
+            umma::tma_load_5d(smem + bf * L::plane, pmap, 0, z0 - 1, y0 - 1, 0, px, pbar + bf);
+            copy_par ^= 1u << bf;
+            used |= 1u << bf;
+        };
+        auto await_plane = [&](int px) {
+            const int bf = (px + NBUF) % NBUF;
+            if (!umma::mbar_wait(pbar + bf, (wait_par >> bf) & 1u, kTcWaitTries)) s_fail = 1;
+            wait_par ^= 1u << bf;
+        };
+        // planes xa-1 .. xa+NBUF-2 (the ring is idle here: the previous run's MMAs are done)
+        if (tid == 0)
+            for (int px = xa - 1; px <= xa + NBUF - 2 && px <= xb; ++px) copy_plane(px);
         for (int x = xa; x <= xb; ++x) {
-            const int i = x - xa;                 // step: tile x issued, tile x-1 written out, plane x+2 staged
-            umma::fence_async_smem();
+            const int i = x - xa;                 // step: tile x issued, tile x-1 written out, plane x+2 started
             umma::fence_before_sync();
             __syncthreads();
             umma::fence_after_sync();
             if (x < xb && tid == 0) {
+                if (i == 0) { await_plane(x - 1); await_plane(x); }
+                await_plane(x + 1);
                 const uint32_t acc = tmem + (uint32_t)(NB * (i & 1));
                 for (int dxy = 0; dxy < 9; ++dxy) {
                     const int dx = dxy / 3, dy = dxy % 3;                  // offset + 1
-                    const uint32_t a0 = s_planes + ((x - 1 + dx) & 3) * L::plane + dy * 512;
+                    const uint32_t a0 = s_planes + ((x - 1 + dx + NBUF) % NBUF) * L::plane + dy * 512;
                     const uint32_t b0 = s_wts + dxy * L::dxy;
 #pragma unroll
                     for (int kk = 0; kk < CIN / 16; ++kk)
@@ -262,30 +247,27 @@ k_conv3d_fwd_tc(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__res
                 }
                 umma::mma_commit(mbar + (i & 1));
             }
-            // Plane x+3's loads go out now and stay in registers for a whole
-            // step; plane x+2 (for tile x+1), loaded one step ago, is stored
-            // once the MMAs of tile x-1, the last reader of that ring buffer,
-            // are done.
-            PlaneRegs<CIN> after;
-            if (x + 3 <= xb) plane_load<CIN>(after, in, x + 3, y0, z0, nx, ny, nz, tid);
             if (i > 0) {
                 const int p = (i - 1) & 1;
-                const bool ok = umma::mbar_wait(mbar + p, issued[p] & 1u, kTcWaitTries);
-                issued[p] += 1;
+                const bool ok = umma::mbar_wait(mbar + p, (mma_par >> p) & 1u, kTcWaitTries) && !s_fail;
+                mma_par ^= 1u << p;
+                // tile x-1, the last reader of plane x-2's buffer, is done: that
+                // buffer takes plane x-2+NBUF now, before the tile is written out
+                if (tid == 0 && x - 2 + NBUF <= xb) copy_plane(x - 2 + NBUF);
                 umma::fence_after_sync();
                 tile_epilogue<COUT, RELU, OUT_F32>(tmem, (uint32_t)(NB * p), ok, out, x - 1, y0, z0, ny, nz, warp,
                                                    lane);
             }
-            if (x + 2 <= xb) {
-                umma::fence_async_smem();
-                plane_store<CIN>(smem + ((x + 2) & 3) * L::plane, next, tid);
-            }
-            next = after;
         }
         umma::fence_before_sync();
         __syncthreads();                       // ring and accumulators free for the next run
         umma::fence_after_sync();
     }
+    // after a wait that gave up, a copy may still be writing shared memory:
+    // wait (bounded) for the last copy into every buffer
+    if (tid == 0 && s_fail)
+        for (int bf = 0; bf < NBUF; ++bf)
+            if ((used >> bf) & 1u) umma::mbar_wait(pbar + bf, ((copy_par >> bf) & 1u) ^ 1u, kTcWaitTries);
     if (warp == 0) umma::tmem_dealloc(tmem, L::tmem_cols);
 }
 
@@ -486,6 +468,22 @@ cudaError_t conv3d_forward(const __nv_bfloat16 *in, const __nv_bfloat16 *wk, voi
                            int cout, bool relu, bool out_f32, cudaStream_t st)
 {
     const int tiles_y = (ny + 3) / 4, tiles_z = (nz + kTileZ - 1) / kTileZ;
+    if (nx < 1 || ny < 1 || nz < 1) return cudaSuccess;
+    if (cin != 16 && cin != 32) return cudaErrorInvalidValue;
+    // Input planes: the activations [x][y][z][cin] viewed as the 5-D tensor
+    // (8 channels, z, y, channel group, x) -- strides 2, 2 cin, 2 cin nz, 16,
+    // 2 cin nz ny bytes -- whose 8 x 32 x 6 x cin/8 x 1 box is one plane buffer.
+    const auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(driver_tensor_map_encoder());
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap planes;
+    const cuuint64_t dims[5] = {8, (cuuint64_t)nz, (cuuint64_t)ny, (cuuint64_t)(cin / 8), (cuuint64_t)nx};
+    const cuuint64_t strides[4] = {(cuuint64_t)cin * 2, (cuuint64_t)nz * cin * 2, 16, (cuuint64_t)ny * nz * cin * 2};
+    const cuuint32_t box[5] = {8, 32, 6, (cuuint32_t)(cin / 8), 1};
+    const cuuint32_t elem[5] = {1, 1, 1, 1, 1};
+    if (enc(&planes, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(in), dims, strides, box, elem,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
 #define TT_CONV_LAUNCH(CI, CO, R, F)                                                                  \
     do {                                                                                              \
         auto kern = k_conv3d_fwd_tc<CI, CO, R, F>;                                                    \
@@ -496,10 +494,9 @@ cudaError_t conv3d_forward(const __nv_bfloat16 *in, const __nv_bfloat16 *wk, voi
         const long long slots = (long long)sm_count() * (sm <= 110u * 1024u ? 2 : 1);                  \
         const long long n_tiles = (long long)nx * tiles_y * tiles_z;                                   \
         const int grid = (int)(n_tiles < slots ? n_tiles : slots);                                     \
-        kern<<<grid, kTcThreads, sm, st>>>(in, wk, out, nx, ny, nz, tiles_y, tiles_z);                \
+        kern<<<grid, kTcThreads, sm, st>>>(planes, wk, out, nx, ny, nz, tiles_y, tiles_z);            \
         return cudaGetLastError();                                                                    \
     } while (0)
-    if (nx < 1 || ny < 1 || nz < 1) return cudaSuccess;
     if (cin == 16 && cout == 32 && relu && !out_f32) TT_CONV_LAUNCH(16, 32, true, false);
     if (cin == 32 && cout == 32 && relu && !out_f32) TT_CONV_LAUNCH(32, 32, true, false);
     if (cin == 32 && cout == 16 && !relu && out_f32) TT_CONV_LAUNCH(32, 16, false, true);

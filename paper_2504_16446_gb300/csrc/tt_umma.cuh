@@ -141,6 +141,17 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int c0,
         : "memory");
 }
 
+// Same for a 5-D tensor map, coordinates (c0, ..., c4), innermost first.
+__device__ __forceinline__ void tma_load_5d(void *dst, const void *tmap, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(mbar))
+        : "memory");
+}
+
 // Makes a tensor map written to global memory by ordinary stores visible to
 // the tensor-copy unit (once per CTA before its first copy).
 __device__ __forceinline__ void tensormap_acquire(const void *tmap)
@@ -179,4 +190,9 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 }
 
 }  // namespace umma
+
+// Host: the driver's tiled tensor-map encoder (cuTensorMapEncodeTiled),
+// looked up once through the runtime; NULL when the driver lacks it.
+void *driver_tensor_map_encoder();
+
 }  // namespace tt
