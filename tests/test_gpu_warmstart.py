@@ -36,7 +36,7 @@ def rel_l2(a, b):
 
 
 @pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 16), (16, 16)])
-@pytest.mark.parametrize("shape", [(5, 7, 37), (2, 4, 32), (9, 3, 20)])
+@pytest.mark.parametrize("shape", [(5, 7, 37), (2, 4, 32), (9, 3, 20), (1, 2, 1), (3, 9, 61)])
 def test_conv_kernels_match_oracle(cin, cout, shape):
     rng = np.random.default_rng(cin + cout + shape[2])
     x = bf16_round(rng.normal(size=shape + (cin,)))
