@@ -674,8 +674,9 @@ def config_oracle_legs(torch, tt, synth):
 def warm_start_time_to_loss(torch, tt, n_test: int, ref_iters: int):
     """The plain FP32 form against the mixed-precision, warm-started form:
     L-BFGS time to (L - L*)/(L0 - L*) <= 1e-3 from zero (FP32 handle) and from
-    the learned warm start (bfloat16-storage handle; inference and the two
-    loss evaluations that scale the prediction included) on held-out 128^3
+    the learned warm start (bfloat16-storage handle), each timed from scratch
+    (the warm row includes its evaluation at zero, the inference and the ray
+    start, one evaluation at the network's output) on held-out 128^3
     phantoms (l_max 4, 240 projections of 128x128 x 16 segments).  The
     network's weights come from the file that the training script writes
     (``python -m paper_2504_16446_gb300.warmstart --save-weights``); without

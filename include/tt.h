@@ -239,6 +239,24 @@ tt_status tt_tv_huber_f64(tt_handle *h, const double *c_dev, double delta, doubl
  * exists.  tt_lbfgs_create evaluates the loss and gradient at c0_dev. */
 tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0_dev, const void *I_dev,
                           const void *W_dev, tt_lbfgs **out);
+/* A state started at the minimiser of the loss along the ray {a u_dev}
+ * (the learned warm start's scaling, Section "Optimization" problem with the
+ * network's output as the direction), at the cost of ONE gradient
+ * evaluation, the one at u_dev.  g0_dev and loss0 are the gradient and loss
+ * at zero from an earlier evaluation (tt_gradient_residual at c = 0,
+ * g0 = -2 A^T W I, loss0 = sum W I^2).  The loss is quadratic along the ray,
+ * L(a u) = a^2 |A u|^2_W - 2 a <A u, W I> + loss0, with <A u, W I> =
+ * -<u, g0>/2 and |A u|^2_W = L(u) - loss0 + 2 <A u, W I>; the state starts at
+ * a* u, a* = <A u, W I> / |A u|^2_W, with loss loss0 - <A u, W I>^2 / |A u|^2_W
+ * and gradient a* g(u) + (1 - a*) g0 (no evaluation at a* u).  If the ray
+ * does not lower the loss (A u = 0, or a non-finite value), the state starts
+ * at zero with (loss0, g0) and *alpha_out = 0.  *alpha_out (may be NULL)
+ * receives a*.  u_dev and g0_dev: [nx][ny][nz][K], the handle's API type,
+ * 16-byte aligned, read only; I_dev / W_dev as for tt_lbfgs_create.  The
+ * state's evaluation counter starts at 1 (the evaluation at u).  Returns
+ * TT_INVALID_ARG for a bad argument, TT_NONFINITE if L(u) is not finite. */
+tt_status tt_lbfgs_create_ray(tt_handle *h, int m, const void *u_dev, const void *g0_dev, double loss0,
+                              const void *I_dev, const void *W_dev, double *alpha_out, tt_lbfgs **out);
 /* One iteration.  c_out_dev (may be NULL) receives the new iterate
  * [nx][ny][nz][K]; *loss_host the new loss; *n_evals_host the number of
  * gradient evaluations used.  On TT_LINESEARCH_FAILED the iterate is

@@ -636,6 +636,77 @@ tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0, const void *I, co
     return TT_OK;
 }
 
+}  // extern "C"
+
+// The loss is quadratic along any ray: L(a u) = a^2 q - 2 a l + L0 with
+// q = |A u|^2_W and l = <A u, W I>.  The gradient at zero, g0 = -2 A^T W I,
+// gives l = -<u, g0> / 2, and one evaluation at u gives q = L(u) - L0 + 2 l
+// and g(u) = 2 A^T W A u + g0.  The minimiser a* = l / q, its loss
+// L0 - l^2 / q and its gradient a* g(u) + (1 - a*) g0 follow without an
+// evaluation at a* u.
+template <typename T>
+static tt_status create_ray(tt_handle *h, int m, const T *u, const T *g0, double L0, const void *I, const void *W,
+                            double *alpha_out, tt_lbfgs **out)
+{
+    tt_lbfgs *st = nullptr;
+    tt_status s = alloc_state(h, m, I, W, &st);
+    if (s != TT_OK) return s;
+    T *x = (T *)st->x, *g = (T *)st->g;
+    const size_t bytes = h->esize() * st->n;
+    double Lu = 0.0;
+    s = tt_grad_enqueue<T>(h, u, (const T *)I, (const T *)W, g);
+    cudaError_t e = cudaSuccess;
+    if (s == TT_OK) e = vec_dot<T>(h, u, g0, st->n, st->part, st->dots, nullptr, 1.0);
+    if (s == TT_OK && e == cudaSuccess)
+        e = cudaMemcpyAsync(st->pinned, st->dots, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (s == TT_OK && e != cudaSuccess) s = cuda_fail(e, "tt_lbfgs_create_ray: <u, g0>");
+    if (s == TT_OK) s = tt_read_loss(h, &Lu);   // synchronises: the dot product is in st->pinned too
+    if (s != TT_OK) { free_state(st); return s; }
+    const double lin = -0.5 * st->pinned[0];
+    const double quad = Lu - L0 + 2.0 * lin;
+    double alpha = 0.0, f = L0;
+    if (quad > 0.0 && std::isfinite(quad) && std::isfinite(lin)) {
+        alpha = lin / quad;
+        f = L0 - lin * lin / quad;
+    }
+    if (alpha != 0.0 && f < L0) {
+        e = vec_axpby<T>(h, x, u, st->n, alpha, nullptr, 0.0);                    // x = a* u
+        if (e == cudaSuccess) e = vec_axpby<T>(h, g, g0, st->n, 1.0 - alpha, nullptr, alpha);   // g = a* g(u) + (1 - a*) g0
+    } else {
+        alpha = 0.0;
+        f = L0;
+        e = cudaMemsetAsync(x, 0, bytes, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g, g0, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    }
+    if (e != cudaSuccess) { free_state(st); return cuda_fail(e, "tt_lbfgs_create_ray: start point"); }
+    st->f = f;
+    s = initial_gram<T>(st);
+    if (s != TT_OK) { free_state(st); return s; }
+    if (alpha_out) *alpha_out = alpha;
+    *out = st;
+    return TT_OK;
+}
+
+extern "C" {
+
+tt_status tt_lbfgs_create_ray(tt_handle *h, int m, const void *u, const void *g0, double loss0, const void *I,
+                              const void *W, double *alpha_out, tt_lbfgs **out)
+{
+    if (!out) { set_error("tt_lbfgs_create_ray: out must not be NULL"); return TT_INVALID_ARG; }
+    *out = nullptr;
+    if (!h || !u || !g0 || !I || m < 1 || m > kMaxM || !std::isfinite(loss0) || loss0 < 0.0) {
+        set_error("tt_lbfgs_create_ray: need a handle, u, g0, I, a finite loss0 >= 0 and 1 <= m <= 64");
+        return TT_INVALID_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(g0) & 15u) != 0) {
+        set_error("tt_lbfgs_create_ray: g0 must be 16-byte aligned");
+        return TT_INVALID_ARG;
+    }
+    return (h->prec != TT_F64)
+               ? create_ray<float>(h, m, (const float *)u, (const float *)g0, loss0, I, W, alpha_out, out)
+               : create_ray<double>(h, m, (const double *)u, (const double *)g0, loss0, I, W, alpha_out, out);
+}
+
 tt_status tt_lbfgs_stats(const tt_lbfgs *st, long long *iterations, long long *evaluations, double *last_step)
 {
     if (!st) { set_error("tt_lbfgs_stats: null state"); return TT_INVALID_ARG; }

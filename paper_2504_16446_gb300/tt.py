@@ -83,6 +83,8 @@ SIGNATURES = {
     "tt_tv_huber": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _D]),
     "tt_tv_huber_f64": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _D]),
     "tt_lbfgs_create": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(_P)]),
+    "tt_lbfgs_create_ray": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_double, _P, _P, _D,
+                                           ctypes.POINTER(_P)]),
     "tt_lbfgs_step": (ctypes.c_int, [_P, _P, _P, _D, ctypes.POINTER(ctypes.c_int)]),
     "tt_lbfgs_get": (ctypes.c_int, [_P, _P, _P, _P, _D]),
     "tt_lbfgs_destroy": (ctypes.c_int, [_P]),
@@ -403,6 +405,29 @@ class LBFGS:
         self.h = handle
         self._keep = (None, I, W)
         self._st = st
+        self.loss = self.get()[2]
+        self._start_log(I, W, log)
+        return self
+
+    @classmethod
+    def from_ray(cls, handle: "Handle", u: torch.Tensor, g0: torch.Tensor, loss0: float, I: torch.Tensor,
+                 W: torch.Tensor | None = None, m: int = 10, log: bool = True) -> "LBFGS":
+        """A state started at the loss minimiser along the ray {a u}, given the
+        gradient g0 and loss loss0 at zero (tt_lbfgs_create_ray: one gradient
+        evaluation, at u).  The chosen a is in .alpha (0: started at zero)."""
+        handle._sync_stream()
+        dt, vs, ds = handle.dtype, handle.volume_shape, handle.data_shape
+        st = _P()
+        alpha = ctypes.c_double(0.0)
+        _check(handle.lib.tt_lbfgs_create_ray(handle._h, int(m), _dptr(u, dt, vs, "u"), _dptr(g0, dt, vs, "g0"),
+                                              float(loss0), _dptr(I, dt, ds, "I"),
+                                              None if W is None else _dptr(W, dt, ds, "W"), ctypes.byref(alpha),
+                                              ctypes.byref(st)), "tt_lbfgs_create_ray")
+        self = cls.__new__(cls)
+        self.h = handle
+        self._keep = (u, I, W)
+        self._st = st
+        self.alpha = alpha.value
         self.loss = self.get()[2]
         self._start_log(I, W, log)
         return self

@@ -172,3 +172,81 @@ def test_lbfgs_checkpoint_resume_continues_exactly(prec, tmp_path):
         tt.LBFGS.restore(h, bad, Id)
     a.close()
     b.close()
+
+
+def _ray_expected(g, st, u, I, W):
+    """Oracle (FP64) start on the ray {a u}: a* = <Au, W I> / <Au, W Au>,
+    and the loss and gradient evaluated at a* u."""
+    B = oracle.basis_matrix(g)
+    Au = oracle.forward(g, u, B)
+    w = np.ones_like(I) if W is None else W
+    alpha = float(np.sum(w * Au * I) / np.sum(w * Au * Au))
+    x = alpha * u
+    f, grad = oracle.gradient_residual(g, x, I, W, B)
+    return alpha, x, f, grad
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_lbfgs_ray_start_matches_the_oracle(prec):
+    """tt_lbfgs_create_ray starts at the loss minimiser along u with the loss
+    and gradient of a direct evaluation there, from one evaluation at u and
+    the gradient at zero."""
+    st, g, I = _problem(4, n=(9, 8, 10), ell_max=4)
+    W = synth.random_weights(st, 5)
+    u = synth.random_volume(st, 6)
+    alpha_ref, x_ref, f_ref, g_ref = _ray_expected(g, st, u, I, W)
+    h = tt.Handle(st, prec)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    Id, Wd, ud = (torch.as_tensor(a, dtype=dt, device="cuda").contiguous() for a in (I, W, u))
+    z = torch.zeros(st.volume_shape, dtype=dt, device="cuda")
+    L0, g0 = h.gradient_residual(z, Id, Wd)
+    opt = tt.LBFGS.from_ray(h, ud, g0, L0, Id, Wd, m=10)
+    x, gr, f = opt.get()
+    tol = 1e-10 if prec == "f64" else 1e-5
+    assert abs(opt.alpha - alpha_ref) <= tol * abs(alpha_ref)
+    assert abs(f - f_ref) <= tol * f_ref
+    rel = lambda a, b: float(np.linalg.norm(a.cpu().numpy().ravel() - b.ravel()) / np.linalg.norm(b.ravel()))
+    assert rel(x, x_ref) <= tol
+    assert rel(gr, g_ref) <= (1e-9 if prec == "f64" else 1e-4)
+    assert opt.stats() == {"iterations": 0, "evaluations": 1, "last_step": 0.0}
+    f_prev = f
+    for _ in range(5):
+        fn, _, status = opt.step()
+        assert status == tt.TT_OK and fn < f_prev
+        f_prev = fn
+
+
+def test_lbfgs_ray_start_recovers_the_scale_of_the_truth():
+    """Noise-free data of a volume c: along u = c / 2 the minimiser is a = 2
+    exactly, with zero loss and zero gradient there."""
+    st, g, _ = _problem(7, n=(8, 9, 8), ell_max=2)
+    truth = synth.random_volume(st, 8)
+    I = oracle.forward(g, truth)
+    h = tt.Handle(st, "f64")
+    Id = torch.as_tensor(I, device="cuda")
+    z = torch.zeros(st.volume_shape, dtype=torch.float64, device="cuda")
+    L0, g0 = h.gradient_residual(z, Id, None)
+    opt = tt.LBFGS.from_ray(h, torch.as_tensor(0.5 * truth, device="cuda"), g0, L0, Id, None)
+    x, gr, f = opt.get()
+    assert abs(opt.alpha - 2.0) <= 1e-12
+    assert f <= 1e-20 * L0
+    assert float(gr.abs().max()) <= 1e-10 * float(g0.abs().max())
+    assert float((x - torch.as_tensor(truth, device="cuda")).abs().max()) <= 1e-12 * float(np.abs(truth).max())
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_lbfgs_ray_start_falls_back_to_zero(prec):
+    """A ray that cannot lower the loss (u = 0) leaves the state at zero with
+    the loss and gradient given for zero, copied unchanged."""
+    st, g, I = _problem(9, n=(8, 8, 8), ell_max=2)
+    h = tt.Handle(st, prec)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    Id = torch.as_tensor(I, dtype=dt, device="cuda")
+    z = torch.zeros(st.volume_shape, dtype=dt, device="cuda")
+    L0, g0 = h.gradient_residual(z, Id, None)
+    opt = tt.LBFGS.from_ray(h, z.clone(), g0, L0, Id, None)
+    x, gr, f = opt.get()
+    assert opt.alpha == 0.0 and f == L0
+    assert torch.equal(gr, g0) and float(x.abs().max()) == 0.0
+    with pytest.raises(tt.TTError):
+        tt.LBFGS.from_ray(h, z, g0, float("nan"), Id, None)

@@ -223,3 +223,27 @@ def test_warm_start_scaling_reports_the_loss_at_its_result():
     assert float(c0.abs().max()) > 0 and Lw < L0
     L_true, _ = h.gradient_residual(c0, I, None, want_grad=False)
     assert abs(L_true - Lw) <= 1e-4 * L0
+
+
+def test_ray_started_solver_agrees_with_the_two_loss_scaling():
+    """warmstart.warm_lbfgs (one evaluation at u through tt_lbfgs_create_ray)
+    starts where warmstart.warm_start's two-loss scaling puts c0, with the
+    same loss."""
+    from paper_2504_16446_gb300 import warmstart
+    st = synth.small_setup(n=(16, 16, 16), nj=16, nk=16, ell_max=4, n_proj=12, n_seg=8, seed=23, offsets=False)
+    h = tt.Handle(st, "f32")
+    ph = synth.ellipsoid_phantom(16, 4, 3, 79)
+    dirs = torch.as_tensor(ph.dirs.reshape(-1, 3), dtype=torch.float32, device="cuda")
+    amps = torch.as_tensor(ph.amps.reshape(-1, 3), dtype=torch.float32, device="cuda")
+    I = h.project(tt.zonal_to_sh(4, dirs, amps).reshape(st.volume_shape).contiguous())
+    z = torch.zeros(st.volume_shape, dtype=torch.float32, device="cuda")
+    L0, g0 = h.gradient_residual(z, I, None)
+    net = tt.WarmStartNet(15, 15, seed=6)
+    c0, Lw = warmstart.warm_start(net, h, I, g0, L0)
+    opt = warmstart.warm_lbfgs(net, h, I, g0, L0)
+    x, _, f = opt.get()
+    assert opt.alpha != 0.0
+    assert float((x - c0).norm() / c0.norm()) <= 1e-4
+    assert abs(f - Lw) <= 1e-4 * L0
+    f1, _, status = opt.step()
+    assert status == tt.TT_OK and f1 < f
