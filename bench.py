@@ -59,7 +59,7 @@ def parse():
                     help="L-BFGS iterations of the reference solve that defines L*")
     ap.add_argument("--cpu-sample-evals", type=float, default=4.0,
                     help="oracle sample size in full-workload gradient evaluations")
-    ap.add_argument("--ws-test", type=int, default=8,
+    ap.add_argument("--ws-test", type=int, default=32,
                     help="held-out 128^3 phantoms of the warm-start time-to-loss comparison (0: skip)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the FP64 cylinder and plywood composite-loss workloads")

@@ -191,11 +191,13 @@ def conv_timing(n: int = 128, reps: int = 20):
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "wsnet_ell64_15to15.npy")
 
 
-def train(n_train: int = 512, epochs: int = 6, target_iters: int = 60, lr: float = 1e-3, seed0: int = 100):
+def train(n_train: int = 512, epochs: int = 6, target_iters: int = 60, lr: float = 1e-3, seed0: int = 100,
+          lr_final: float | None = None):
     """Trains the network on n_train seeded 6-ellipsoid phantoms of the 64^3
     workload (l_max 4, 120 projections of 64x64 x 16 segments): input g0 =
-    grad L(0), target = plain L-BFGS after target_iters iterations.
-    Returns (net, info)."""
+    grad L(0), target = plain L-BFGS after target_iters iterations.  The
+    Adam step size is lr throughout, or with lr_final given, decays from lr
+    to lr_final along a half cosine over the epochs.  Returns (net, info)."""
     st_tr = synth.workload("ell64")
     h_tr = tt.Handle(st_tr, "f32")
     z_tr = torch.zeros(st_tr.volume_shape, dtype=torch.float32, device="cuda")
@@ -212,14 +214,17 @@ def train(n_train: int = 512, epochs: int = 6, target_iters: int = 60, lr: float
     t0 = time.perf_counter()
     losses = []
     for epoch in range(epochs):
+        lr_e = lr
+        if lr_final is not None and epochs > 1:
+            lr_e = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * epoch / (epochs - 1)))
         order = np.random.default_rng(epoch).permutation(len(data))
-        ep = [net.train_step(data[i][0], data[i][1], data[i][2], lr, out_scale=data[i][3]) for i in order]
+        ep = [net.train_step(data[i][0], data[i][1], data[i][2], lr_e, out_scale=data[i][3]) for i in order]
         losses.append(float(np.mean(ep)))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     h_tr.close()
     info = {"workload": "64^3, l_max 4, 120 x 64x64 x 16, 6-ellipsoid phantoms, seeds %d.." % seed0,
-            "samples": n_train, "epochs": epochs, "target_iters": target_iters,
+            "samples": n_train, "epochs": epochs, "target_iters": target_iters, "lr": lr, "lr_final": lr_final,
             "data_seconds": t_data, "train_seconds": t_train, "epoch_mean_loss": losses}
     return net, info
 
@@ -291,10 +296,12 @@ def main(argv=None):
                     help="only time the forward convolutions on an N^3 volume and exit")
     ap.add_argument("--train", type=int, default=512)
     ap.add_argument("--test", type=int, default=32)
-    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--epochs", type=int, default=100)
     ap.add_argument("--target-iters", type=int, default=60, help="plain L-BFGS iterations of a training target")
     ap.add_argument("--ref-iters", type=int, default=150, help="L-BFGS iterations defining L* of a test phantom")
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr-final", type=float, default=5e-5,
+                    help="decay the step size from --lr to this value along a half cosine (0 or less: constant)")
     ap.add_argument("--save-weights", default="", metavar="PATH",
                     help="write the trained weights (float32 .npy) to PATH")
     ap.add_argument("--load-weights", default="", metavar="PATH",
@@ -307,7 +314,8 @@ def main(argv=None):
     if args.load_weights:
         net, info = load_net(args.load_weights), {"weights": args.load_weights}
     else:
-        net, info = train(args.train, args.epochs, args.target_iters, args.lr)
+        net, info = train(args.train, args.epochs, args.target_iters, args.lr,
+                          lr_final=args.lr_final if args.lr_final > 0 else None)
     if args.save_weights:
         os.makedirs(os.path.dirname(os.path.abspath(args.save_weights)), exist_ok=True)
         np.save(args.save_weights, net.weights())
