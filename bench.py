@@ -148,10 +148,9 @@ def paper_shaped(torch, tt, synth, flush, steps: int = 20):
         ct = (torch.randn(st.volume_shape, device="cuda", generator=gen).abs() * 0.1).contiguous()
         It = h.project(ct)
         It = (It + 0.01 * float(It.std()) * torch.randn(It.shape, device="cuda", generator=gen)).contiguous()
-        z = torch.zeros_like(ct)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        opt = tt.LBFGS(h, z, It, None, m=10, log=False)
+        opt = tt.LBFGS(h, None, It, None, m=10, log=False)     # from zero
         iters, evals = 0, 1
         for _ in range(20):
             _, ne, status = opt.step()
@@ -376,8 +375,7 @@ def make_inputs(st, torch, tt, synth):
 
 def reference_loss(h, I, W, torch, tt, ref_iters: int):
     """(L0, L*) of the plain FP32 solve: L* = loss after ref_iters L-BFGS iterations."""
-    z = torch.zeros(h.volume_shape, dtype=torch.float32, device="cuda")
-    ref = tt.LBFGS(h, z, I, W, m=10, log=False)
+    ref = tt.LBFGS(h, None, I, W, m=10, log=False)          # from zero
     L0 = ref.loss
     for _ in range(ref_iters):
         _, _, st = ref.step()
@@ -395,10 +393,9 @@ def time_to_loss(h, I, W, torch, tt, ref_iters: int, target: float = 1e-3, L0_Ls
     iterations).  The loss of a reduced-precision handle is its own FP64 sum
     of its residuals."""
     L0, Lstar = L0_Lstar if L0_Lstar else reference_loss(h, I, W, torch, tt, ref_iters)
-    z = torch.zeros(h.volume_shape, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    opt = tt.LBFGS(h, z, I, W, m=10, log=False)
+    opt = tt.LBFGS(h, None, I, W, m=10, log=False)          # from zero
     iters, evals = 0, 1
     while (opt.loss - Lstar) > target * (L0 - Lstar) and iters < ref_iters:
         _, ne, st = opt.step()
@@ -449,10 +446,9 @@ def noise_free_residual(h, c_true, torch, tt, target: float = 1e-3, max_iter: in
     (computed from the loss, W = 1).  Wall time, iterations, evaluations."""
     I = h.project(c_true)
     nI = float(torch.linalg.vector_norm(I.double()))
-    z = torch.zeros(h.volume_shape, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    opt = tt.LBFGS(h, z, I, None, m=10, log=False)
+    opt = tt.LBFGS(h, None, I, None, m=10, log=False)       # from zero
     it, ev = 0, 1
     while opt.loss ** 0.5 > target * nI and it < max_iter:
         _, ne, st_ = opt.step()
@@ -565,7 +561,7 @@ def measure_configs(torch, tt, synth, flush):
     ms_eval = _timed(torch, lambda: h.gradient_residual(z, I, None, out=g), flush, 50)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    opt = tt.LBFGS(h, z, I, None, m=10, log=False)
+    opt = tt.LBFGS(h, None, I, None, m=10, log=False)       # from zero
     L0 = opt.loss
     iters, evals = 0, 1
     for _ in range(20):

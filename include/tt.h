@@ -188,6 +188,12 @@ tt_status tt_adjoint_f64(tt_handle *h, const double *R_dev, double *g_dev);
  *   r = A c - I,  *loss_host = sum W r^2 (FP64 accumulation),
  *   g_dev = 2 A^T (W r).
  * W_dev may be NULL (all weights 1).  g_dev may be NULL (loss only).
+ * c_dev may be NULL for c = 0: then *loss_host = sum W I^2 and g_dev =
+ * -2 A^T (W I), the back-projection of the data, with the same results as
+ * an all-zero c_dev, bit for bit, but without the forward projection (its
+ * march over a zero volume is skipped; the contraction, residual and
+ * back-contraction run as usual) -- the first evaluation of every solve
+ * from zero and the learned warm start's input.
  * loss_host is a HOST pointer.  The call returns as soon as the loss is
  * known: with g_dev the adjoint publishes it in a page-locked slot when it
  * starts and may still be running on the handle's stream when the call
@@ -236,7 +242,9 @@ tt_status tt_tv_huber_f64(tt_handle *h, const double *c_dev, double delta, doubl
  * iteration); dot products of float vectors use compensated FP32 (Dot2)
  * accumulation within a CTA and FP64 across CTAs.  I_dev / W_dev (W may be NULL) are
  * referenced, not copied: keep them alive and unchanged while the state
- * exists.  tt_lbfgs_create evaluates the loss and gradient at c0_dev. */
+ * exists.  tt_lbfgs_create evaluates the loss and gradient at c0_dev;
+ * c0_dev may be NULL to start at zero (that evaluation then skips the
+ * forward projection, as tt_gradient_residual does for c_dev == NULL). */
 tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0_dev, const void *I_dev,
                           const void *W_dev, tt_lbfgs **out);
 /* A state started at the minimiser of the loss along the ray {a u_dev}
@@ -253,8 +261,12 @@ tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0_dev, const void *I
  * at zero with (loss0, g0) and *alpha_out = 0.  *alpha_out (may be NULL)
  * receives a*.  u_dev and g0_dev: [nx][ny][nz][K], the handle's API type,
  * 16-byte aligned, read only; I_dev / W_dev as for tt_lbfgs_create.  The
- * state's evaluation counter starts at 1 (the evaluation at u).  Returns
- * TT_INVALID_ARG for a bad argument, TT_NONFINITE if L(u) is not finite. */
+ * state's evaluation counter starts at 1 (the evaluation at u).  On a
+ * handle with 2-byte volume storage (TT_BF16, TT_F16) the evaluation rounds
+ * the volume it projects, so the start's loss and gradient differ from an
+ * evaluation at a* u by that rounding (relative 2^-9 / 2^-12 of the A u
+ * terms), as every result of such a handle does.  Returns TT_INVALID_ARG for
+ * a bad argument, TT_NONFINITE if L(u) is not finite. */
 tt_status tt_lbfgs_create_ray(tt_handle *h, int m, const void *u_dev, const void *g0_dev, double loss0,
                               const void *I_dev, const void *W_dev, double *alpha_out, tt_lbfgs **out);
 /* One iteration.  c_out_dev (may be NULL) receives the new iterate

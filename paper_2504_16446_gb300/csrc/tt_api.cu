@@ -561,14 +561,38 @@ static tt_status adjoint_impl(tt_handle *h, const T *R, T *g)
 using namespace tt;
 
 // Enqueues the gradient-residual evaluation; the loss lands in h->loss_dev.
+// While in scope with on = true: the forward launcher projects a zero volume
+// (h->zero_volume), which always takes the L1 kernel, so the loss reduction
+// reads that kernel's number of partials whichever forward kernel is chosen.
+struct ZeroVolume {
+    tt_handle *h;
+    long long saved;
+    ZeroVolume(tt_handle *h_, bool on) : h(h_), saved(h_->n_fwd_ctas)
+    {
+        if (on) {
+            h->zero_volume = true;
+            h->n_fwd_ctas = forward_ctas(h, false);
+        }
+    }
+    ~ZeroVolume()
+    {
+        h->zero_volume = false;
+        h->n_fwd_ctas = saved;
+    }
+};
+
 template <typename T>
 tt_status tt_grad_enqueue(tt_handle *h, const T *c, const T *I, const T *W, T *g)
 {
-    if (bad_ptr(c) || bad_ptr(I) || (W && bad_ptr(W)) || (g && bad_ptr(g)))
-        return invalid("tt_gradient_residual: device pointers must be non-null (W, g may be NULL) and 16-byte aligned");
+    if ((c && bad_ptr(c)) || bad_ptr(I) || (W && bad_ptr(W)) || (g && bad_ptr(g)))
+        return invalid("tt_gradient_residual: device pointers must be non-null (c, W, g may be NULL) and 16-byte aligned");
     return with_storage<T>(h, [&]<typename S>() -> tt_status {
         const ProfChain chain(h);   // pack, forward and adjoint run back to back
-        TT_CUDA((launch_pack<T, S>(h, c)), "pack");
+        // c == NULL: the volume is zero; nothing is packed and the forward
+        // kernel skips its march (every projection is exactly zero), so the
+        // evaluation is the back-projection of the data alone
+        if (c) TT_CUDA((launch_pack<T, S>(h, c)), "pack");
+        const ZeroVolume zero(h, c == nullptr);
         TT_CUDA((launch_forward<T, S>(h, nullptr, I, W, true)), "forward");
         // the adjoint's first CTA reduces the loss partials; without a
         // gradient a one-CTA reduction does

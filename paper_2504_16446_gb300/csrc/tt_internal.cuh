@@ -170,6 +170,7 @@ struct tt_handle {
     // and a bilinear tap pair along it is one contiguous 2*KP-element piece.
     void *cpad = nullptr;
     long long cpad_origin = 0;           // voxel offset of (0,0,0) in cpad
+    bool zero_volume = false;            // set around a forward launch whose volume is zero (not packed)
     bool xcopy = false;                  // the x-innermost copy exists
     long long pad_vox = 0;               // voxels of one padded copy
     long long cpadx_origin = 0;          // voxel offset of (0,0,0) in the x-innermost copy (from its start)

@@ -423,6 +423,7 @@ k_forward(const ProjGeom *__restrict__ geo, const S *__restrict__ cpad /* interi
     clip_planes<T>(vr, vp, Nv, lo, hi);
     int plo = valid ? max(0, (int)floor(lo)) : 1;
     int phi = valid ? min(P.Nm - 1, (int)ceil(hi)) : 0;
+    if (cpad == nullptr) phi = plo - 1;   // a zero volume: every ray sum is exactly zero, nothing to march
 
     // The march reads bilinear taps in pairs along v, the innermost axis of
     // the volume copy this projection reads (sv == 1): rows (iu, iv) and
@@ -1094,11 +1095,13 @@ cudaError_t launch_forward_L(tt_handle *h, T *Iout, const T *I, const T *W, bool
     const long long vol_bytes = (long long)(h->N[0] + 4) * (h->N[1] + 4) * (h->N[2] + 4) * KP * sizeof(S);
     const int slab = vol_bytes > (64LL << 20) ? 1 : 0;
     const T *Bp = (const T *)h->Bp;
-    const S *cpad = (const S *)h->cpad + h->cpad_origin * KP;
-    const S *cpadx = h->xcopy ? (const S *)h->cpad + (h->pad_vox + h->cpadx_origin) * KP : nullptr;
+    // h->zero_volume: the volume is zero (no packed copy); the kernel gets no
+    // volume and marches nothing
+    const S *cpad = h->zero_volume ? nullptr : (const S *)h->cpad + h->cpad_origin * KP;
+    const S *cpadx = (h->xcopy && !h->zero_volume) ? (const S *)h->cpad + (h->pad_vox + h->cpadx_origin) * KP : nullptr;
     cudaEvent_t ev;
     if constexpr (std::is_same<T, float>::value && std::is_same<S, float>::value && KP == 16) {
-        if (h->fwd_staged) {
+        if (h->fwd_staged && !h->zero_volume) {
             const int tiles_k = (h->nk + kStTK - 1) / kStTK, tiles_j = (h->nj + kStTJ - 1) / kStTJ;
             const dim3 grid = slab ? dim3(tiles_k * ns, tiles_j) : dim3(tiles_k * tiles_j, ns);
             const size_t smem = staged_forward_smem(h);

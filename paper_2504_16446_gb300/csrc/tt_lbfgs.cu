@@ -617,18 +617,22 @@ tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0, const void *I, co
 {
     if (!out) { set_error("tt_lbfgs_create: out must not be NULL"); return TT_INVALID_ARG; }
     *out = nullptr;
-    if (!h || !c0 || !I || m < 1 || m > kMaxM) {
-        set_error("tt_lbfgs_create: need a handle, c0, I and 1 <= m <= 64");
+    if (!h || !I || m < 1 || m > kMaxM) {
+        set_error("tt_lbfgs_create: need a handle, I and 1 <= m <= 64");
         return TT_INVALID_ARG;
     }
     tt_lbfgs *st = nullptr;
     tt_status s = alloc_state(h, m, I, W, &st);
     if (s != TT_OK) return s;
-    cudaError_t e = cudaMemcpyAsync(st->x, c0, h->esize() * st->n, cudaMemcpyDeviceToDevice, h->stream);
+    // c0 == NULL: start at zero, where the evaluation needs no forward march
+    const size_t bytes = h->esize() * st->n;
+    cudaError_t e = c0 ? cudaMemcpyAsync(st->x, c0, bytes, cudaMemcpyDeviceToDevice, h->stream)
+                       : cudaMemsetAsync(st->x, 0, bytes, h->stream);
     if (e != cudaSuccess) { free_state(st); return cuda_fail(e, "tt_lbfgs_create"); }
+    const void *xc = c0 ? st->x : nullptr;
     s = (h->prec != TT_F64)
-            ? tt_grad_enqueue<float>(h, (const float *)st->x, (const float *)I, (const float *)W, (float *)st->g)
-            : tt_grad_enqueue<double>(h, (const double *)st->x, (const double *)I, (const double *)W, (double *)st->g);
+            ? tt_grad_enqueue<float>(h, (const float *)xc, (const float *)I, (const float *)W, (float *)st->g)
+            : tt_grad_enqueue<double>(h, (const double *)xc, (const double *)I, (const double *)W, (double *)st->g);
     if (s == TT_OK) s = tt_read_loss(h, &st->f);
     if (s == TT_OK) s = (h->prec != TT_F64) ? initial_gram<float>(st) : initial_gram<double>(st);
     if (s != TT_OK) { free_state(st); return s; }

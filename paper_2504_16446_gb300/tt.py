@@ -258,14 +258,16 @@ class Handle:
         return out
 
     def gradient_residual(self, c, I, W=None, want_grad=True, out=None, check=True):
-        """(loss, grad): loss = sum W (A c - I)^2, grad = 2 A^T (W (A c - I))."""
+        """(loss, grad): loss = sum W (A c - I)^2, grad = 2 A^T (W (A c - I)).
+        c = None means c = 0 (the back-projection of the data, without a
+        forward projection)."""
         self._sync_stream()
         g = None
         if want_grad:
-            g = torch.empty(self.volume_shape, dtype=self.dtype, device=c.device) if out is None else out
+            g = torch.empty(self.volume_shape, dtype=self.dtype, device=I.device) if out is None else out
         loss = ctypes.c_double(0.0)
         fn = getattr(self.lib, "tt_gradient_residual" + self._sfx)
-        st = fn(self._h, _dptr(c, self.dtype, self.volume_shape, "c"),
+        st = fn(self._h, None if c is None else _dptr(c, self.dtype, self.volume_shape, "c"),
                 _dptr(I, self.dtype, self.data_shape, "I"),
                 None if W is None else _dptr(W, self.dtype, self.data_shape, "W"),
                 None if g is None else _dptr(g, self.dtype, self.volume_shape, "g"),
@@ -349,14 +351,16 @@ class Handle:
 class LBFGS:
     """Device-resident L-BFGS on a Handle (tt_lbfgs_*)."""
 
-    def __init__(self, handle: Handle, c0: torch.Tensor, I: torch.Tensor, W: torch.Tensor | None = None, m: int = 10,
-                 log: bool = True):
+    def __init__(self, handle: Handle, c0: torch.Tensor | None, I: torch.Tensor, W: torch.Tensor | None = None,
+                 m: int = 10, log: bool = True):
+        """c0 = None starts at zero (its evaluation skips the forward projection)."""
         self.h = handle
         handle._sync_stream()
         self._keep = (c0, I, W)
         st = _P()
         dt, vs, ds = handle.dtype, handle.volume_shape, handle.data_shape
-        _check(handle.lib.tt_lbfgs_create(handle._h, int(m), _dptr(c0, dt, vs, "c0"), _dptr(I, dt, ds, "I"),
+        _check(handle.lib.tt_lbfgs_create(handle._h, int(m), None if c0 is None else _dptr(c0, dt, vs, "c0"),
+                                          _dptr(I, dt, ds, "I"),
                                           None if W is None else _dptr(W, dt, ds, "W"), ctypes.byref(st)),
                "tt_lbfgs_create")
         self._st = st

@@ -54,6 +54,29 @@ def test_large_workloads_on_projection_subsets(name, proj):
     assert rel_l2(gg.cpu().numpy(), g_ref) <= TOL
 
 
+@pytest.mark.parametrize("name,proj", [("ell128c16", [0, 101, 239]), ("paper247_l2", [0, 123, 246]),
+                                       ("paper247_l4", [7, 200]), ("paper247_l8", [50, 180])])
+def test_timed_workloads_on_projection_subsets(name, proj):
+    """The held-out test geometry of the warm start (128^3, l_max 4, 16
+    segments: the slab-ordered forward at K = 15) and the paper dataset's
+    shape (55 x 65 x 55 volume, 65 x 55 pixels, 8 segments, l_max 2 / 4 /
+    8: a non-cubic volume and detector) on projection subsets, random
+    iterate and data, with and without weights."""
+    st = synth.workload(name).subset(proj)
+    g = oracle_geometry(st)
+    c = synth.random_volume(st, 41).astype(np.float32)
+    I = synth.random_data(st, 42).astype(np.float32) + 1.0
+    W = synth.random_weights(st, 43).astype(np.float32)
+    h = tt.Handle(st, "f32")
+    for Wi in (None, W):
+        loss_ref, g_ref = oracle.gradient_residual(g, c.astype(np.float64), I.astype(np.float64),
+                                                   None if Wi is None else Wi.astype(np.float64))
+        loss, gg = h.gradient_residual(torch.as_tensor(c, device="cuda"), torch.as_tensor(I, device="cuda"),
+                                       None if Wi is None else torch.as_tensor(Wi, device="cuda"))
+        assert abs(loss - loss_ref) <= TOL * loss_ref
+        assert rel_l2(gg.cpu().numpy(), g_ref) <= TOL
+
+
 def test_ell64_adjoint_identity_fp32():
     st = synth.workload("ell64")
     h = tt.Handle(st, "f32")

@@ -250,3 +250,48 @@ def test_lbfgs_ray_start_falls_back_to_zero(prec):
     assert torch.equal(gr, g0) and float(x.abs().max()) == 0.0
     with pytest.raises(tt.TTError):
         tt.LBFGS.from_ray(h, z, g0, float("nan"), Id, None)
+
+
+def test_lbfgs_ray_start_on_bfloat16_storage():
+    """On a bfloat16-storage handle (the warm-started form's solver) the ray
+    start agrees with the oracle's to the storage rounding -- relative to the
+    loss and gradient at zero, the scale of the A u terms it rounds -- and
+    the solver descends from it."""
+    st, g, I = _problem(11, n=(10, 9, 8), ell_max=4)
+    u = synth.random_volume(st, 12)
+    alpha_ref, x_ref, f_ref, g_ref = _ray_expected(g, st, u, I, None)
+    h = tt.Handle(st, "bf16")
+    Id, ud = (torch.as_tensor(a, dtype=torch.float32, device="cuda").contiguous() for a in (I, u))
+    z = torch.zeros(st.volume_shape, dtype=torch.float32, device="cuda")
+    L0, g0 = h.gradient_residual(z, Id, None)
+    opt = tt.LBFGS.from_ray(h, ud, g0, L0, Id, None)
+    x, gr, f = opt.get()
+    assert abs(opt.alpha - alpha_ref) <= 5e-3 * abs(alpha_ref)
+    assert abs(f - f_ref) <= 5e-3 * L0
+    g0n = float(np.linalg.norm(g0.cpu().numpy().ravel()))
+    assert float(np.linalg.norm(gr.cpu().numpy().ravel() - g_ref.ravel())) <= 5e-3 * g0n
+    f_prev = f
+    for _ in range(3):
+        fn, _, status = opt.step()
+        assert status == tt.TT_OK and fn < f_prev
+        f_prev = fn
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_lbfgs_null_start_is_the_zero_start(prec):
+    """c0 = NULL starts at zero with the evaluation that skips the forward
+    projection; the iterates are those of an all-zero c0, bit for bit."""
+    st, g, I = _problem(13, n=(9, 9, 8), ell_max=4)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    h = tt.Handle(st, prec)
+    Id = torch.as_tensor(I, dtype=dt, device="cuda")
+    a = tt.LBFGS(h, torch.zeros(st.volume_shape, dtype=dt, device="cuda"), Id, None, m=5)
+    b = tt.LBFGS(h, None, Id, None, m=5)
+    assert a.loss == b.loss
+    for _ in range(6):
+        fa, na, sa = a.step()
+        fb, nb, sb = b.step()
+        assert (fa, na, sa) == (fb, nb, sb)
+    xa, ga, _ = a.get()
+    xb, gb, _ = b.get()
+    assert torch.equal(xa, xb) and torch.equal(ga, gb)

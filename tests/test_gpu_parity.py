@@ -336,3 +336,34 @@ def test_degenerate_sizes():
     assert float(torch.abs(h2.project(dev(synth.random_volume(st2, 1), torch.float32))).max()) == 0.0
     assert float(torch.abs(g2).max()) == 0.0
     assert abs(loss2 - float(torch.sum(I2.double() ** 2))) <= 1e-6 * loss2
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64", "bf16"])
+def test_gradient_at_zero_without_a_volume(prec):
+    """c = NULL evaluates at c = 0 without projecting a volume (the forward
+    kernel marches nothing): loss sum W I^2 and gradient -2 A^T W I, bit for
+    bit those of an all-zero volume, with and without weights.  With the
+    staged forward kernel selected the zero volume still takes the L1
+    kernel, whose gradients the staged one matches bit for bit (its loss
+    partials are summed over other ray tiles, so the loss only to 1e-12)."""
+    st = synth.small_setup(n=(12, 10, 11), nj=12, nk=11, ell_max=4, n_proj=9, n_seg=8, seed=17)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    I = dev(synth.random_data(st, 18), dt)
+    W = dev(synth.random_weights(st, 19), dt)
+    z = torch.zeros(st.volume_shape, dtype=dt, device="cuda")
+    h = tt.Handle(st, prec)
+    kinds = ["l1", "staged"] if prec == "f32" else ["auto"]
+    for kind in kinds:
+        h.set_forward_kernel(kind)
+        for Wi in (None, W):
+            loss_z, g_z = h.gradient_residual(z, I, Wi)
+            loss_n, g_n = h.gradient_residual(None, I, Wi)
+            loss_only, _ = h.gradient_residual(None, I, Wi, want_grad=False)
+            if kind == "staged":
+                assert abs(loss_n - loss_z) <= 1e-12 * loss_z
+            else:
+                assert loss_n == loss_z
+            assert loss_only == loss_n
+            assert torch.equal(g_n, g_z)
+            Wd = torch.ones_like(I) if Wi is None else Wi
+            assert abs(loss_n - float((Wd.double() * I.double() ** 2).sum())) <= 1e-6 * loss_n
