@@ -466,12 +466,13 @@ def noise_free_residual(h, c_true, torch, tt, target: float = 1e-3, max_iter: in
 
 def measure_forms(torch, tt, synth, flush, steps: int = 20):
     """ms per gradient evaluation of the FP32, bfloat16- and float16-storage
-    forms on the 64^3 (l_max 4) and 128^3 (l_max 8, 240 x 128^2 x 8) workloads,
+    forms on the 64^3 (l_max 4), the warm start's 128^3 test geometry (l_max
+    4, 240 x 128^2 x 16) and the 128^3 (l_max 8, 240 x 128^2 x 8) workloads,
     and at l_max 4 the FP32 form with the staged forward march
     (tt_set_forward_kernel 2) as "f32_staged"; random O(1) volume and data, L2
     flushed between evaluations."""
     res = {}
-    for wl in ("ell64", "ell128"):
+    for wl in ("ell64", "ell128c16", "ell128"):
         st = synth.workload(wl)
         gen = torch.Generator(device="cuda")
         gen.manual_seed(7)
