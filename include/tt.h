@@ -247,10 +247,10 @@ tt_status tt_tv_huber_f64(tt_handle *h, const double *c_dev, double delta, doubl
  * forward projection, as tt_gradient_residual does for c_dev == NULL). */
 tt_status tt_lbfgs_create(tt_handle *h, int m, const void *c0_dev, const void *I_dev,
                           const void *W_dev, tt_lbfgs **out);
-/* A state started at the minimiser of the loss along the ray {a u_dev}
- * (the learned warm start's scaling, Section "Optimization" problem with the
- * network's output as the direction), at the cost of ONE gradient
- * evaluation, the one at u_dev.  g0_dev and loss0 are the gradient and loss
+/* A state started at the minimiser of the loss (Section "Optimization")
+ * along the ray {a u_dev}, at the cost of ONE gradient evaluation, the one
+ * at u_dev: the learned warm start scales the network's output u_dev this
+ * way (the paper has no warm start; this entry point serves it).  g0_dev and loss0 are the gradient and loss
  * at zero from an earlier evaluation (tt_gradient_residual at c = 0,
  * g0 = -2 A^T W I, loss0 = sum W I^2).  The loss is quadratic along the ray,
  * L(a u) = a^2 |A u|^2_W - 2 a <A u, W I> + loss0, with <A u, W I> =

@@ -560,7 +560,6 @@ static tt_status adjoint_impl(tt_handle *h, const T *R, T *g)
 
 using namespace tt;
 
-// Enqueues the gradient-residual evaluation; the loss lands in h->loss_dev.
 // While in scope with on = true: the forward launcher projects a zero volume
 // (h->zero_volume), which always takes the L1 kernel, so the loss reduction
 // reads that kernel's number of partials whichever forward kernel is chosen.
@@ -581,6 +580,7 @@ struct ZeroVolume {
     }
 };
 
+// Enqueues the gradient-residual evaluation; the loss lands in h->loss_dev.
 template <typename T>
 tt_status tt_grad_enqueue(tt_handle *h, const T *c, const T *I, const T *W, T *g)
 {
