@@ -828,7 +828,11 @@ def run_ours(args):
         "clocks": clocks,
         "loss": losses[-1],
     }
-    if not args.no_time_to_loss:
+    # The single-GPU legs below (time to loss, standalone kernels, the other
+    # workloads, the precision forms) are reported on the one-GPU line only:
+    # under torchrun every rank would repeat them while holding its GPU.
+    aux = world == 1
+    if aux and not args.no_time_to_loss:
         ref = reference_loss(h, I, W, torch, tt, args.ttl_ref_iters)
         out["time_to_loss"] = {"plain_f32": time_to_loss(h, I, W, torch, tt, args.ttl_ref_iters, L0_Lstar=ref)}
         hb = tt.Handle(st, "bf16")
@@ -842,10 +846,11 @@ def run_ours(args):
                 out["time_to_loss"][key] = dict(ws[key], samples=ws["samples"], workload=ws["workload"],
                                                 criterion=ws["criterion"])
             out["time_to_loss"]["warm_start"] = ws
-    out["standalone"] = standalone(h, c, I, torch, flush)
-    if not args.no_configs:
+    if aux:
+        out["standalone"] = standalone(h, c, I, torch, flush)
+    if aux and not args.no_configs:
         out["configs"] = measure_configs(torch, tt, synth, flush)
-    if not args.no_forms:
+    if aux and not args.no_forms:
         out["forms"] = measure_forms(torch, tt, synth, flush)
         out["paper_shaped"] = paper_shaped(torch, tt, synth, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
