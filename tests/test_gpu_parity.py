@@ -367,3 +367,18 @@ def test_gradient_at_zero_without_a_volume(prec):
             assert torch.equal(g_n, g_z)
             Wd = torch.ones_like(I) if Wi is None else Wi
             assert abs(loss_n - float((Wd.double() * I.double() ** 2).sum())) <= 1e-6 * loss_n
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+def test_host_entry_point_on_two_byte_storage(prec):
+    """The host-buffer entry point on a 2-byte-storage handle: the same loss
+    and gradient as the device entry point, bit for bit."""
+    st = synth.small_setup(n=(11, 10, 12), nj=12, nk=11, ell_max=4, n_proj=9, n_seg=8, seed=27)
+    c = synth.random_volume(st, 1).astype(np.float32)
+    I = synth.random_data(st, 2).astype(np.float32)
+    W = synth.random_weights(st, 3).astype(np.float32)
+    h = tt.Handle(st, prec)
+    loss_d, g_d = h.gradient_residual(dev(c, torch.float32), dev(I, torch.float32), dev(W, torch.float32))
+    loss_h, g_h = h.gradient_residual_host(c, I, W)
+    assert loss_h == loss_d
+    np.testing.assert_array_equal(g_h, g_d.cpu().numpy())

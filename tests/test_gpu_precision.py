@@ -86,3 +86,27 @@ def test_bf16_lbfgs_decreases_and_tracks_fp32():
         assert all(b <= a for a, b in zip(losses, losses[1:]))
         runs[prec] = losses
     assert abs(runs["bf16"][-1] - runs["f32"][-1]) <= 0.05 * runs["f32"][0]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+def test_reduced_precision_on_the_warm_start_test_geometry(prec):
+    """128^3, l_max 4 (K = 15), 16 segments: the geometry of the held-out
+    phantoms the warm-started bfloat16 solve is timed on (3 projections),
+    the first held-out phantom, a generic iterate, Poisson data."""
+    st = synth.workload("ell128c16").subset([0, 101, 239])
+    g = oracle_geometry(st)
+    ph = synth.ellipsoid_phantom(128, 4, 6, 5000)
+    c_true = oracle.zonal_to_sh(4, ph.dirs.reshape(-1, 3), ph.amps.reshape(-1, 3)).reshape(st.volume_shape)
+    I = synth.poisson_counts(oracle.forward(g, c_true), 1e4, seed=3)
+    c = (0.6 * c_true + 0.05 * synth.random_volume(st, 4)).astype(np.float32)
+    loss_ref, grad_ref = oracle.gradient_residual(g, c.astype(np.float64), I)
+    h = tt.Handle(st, prec)
+    cd = torch.as_tensor(c, device="cuda")
+    loss, grad = h.gradient_residual(cd, torch.as_tensor(I.astype(np.float32), device="cuda"))
+    e_proj = rel_l2(h.project(cd).cpu().numpy(), oracle.forward(g, c.astype(np.float64)))
+    e_grad = rel_l2(grad.cpu().numpy(), grad_ref)
+    e_loss = abs(loss - loss_ref) / loss_ref
+    print(f"{prec}: projection {e_proj:.2e}, gradient {e_grad:.2e}, loss {e_loss:.2e}")
+    for e in (e_proj, e_grad):
+        assert 1e-5 < e <= TOL[prec]
+    assert e_loss <= 10 * TOL[prec]
