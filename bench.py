@@ -607,6 +607,22 @@ def measure_configs(torch, tt, synth, flush):
                                "ms_per_eval": ms_comp, "evals_per_s": 1e3 / ms_comp,
                                "regularisers_ms": ms_reg, "regulariser_share": ms_reg / ms_comp}
     h.close()
+    # 128^3, l_max 8, 240 projections of 128x128 x 8 segments: the precision
+    # form (2-byte volume storage) against plain FP32, L-BFGS from zero to a
+    # 1e-3 excess loss over the FP32 solve's L* (150 iterations)
+    st = synth.workload("ell128")
+    h = tt.Handle(st, "f32")
+    I, _ = config_inputs("ell128", torch, tt, synth, h, ("poisson", 1e4), 2)
+    ref = reference_loss(h, I, None, torch, tt, 150)
+    row = {"workload": "128^3, l_max 8 (K=45), 240 projections (24 rotations x 10 tilts 0-45 deg) of 128x128 x 8 "
+                       "segments, 12-ellipsoid phantom (seed 2), Poisson counts at mean 1e4",
+           "f32": time_to_loss(h, I, None, torch, tt, 150, L0_Lstar=ref)}
+    h.close()
+    for prec in ("bf16", "f16"):
+        hp = tt.Handle(st, prec)
+        row[prec] = time_to_loss(hp, I, None, torch, tt, 150, L0_Lstar=ref)
+        hp.close()
+    out["ell128_precision"] = row
     return out
 
 
@@ -665,6 +681,25 @@ def config_oracle_legs(torch, tt, synth):
                                "inputs": "projections 0, 61, 133; random volume N(0,1) seed 33, data 100 + N(0,1) "
                                          "seed 34"}
     h.close()
+    # precision forms at 128^3, l_max 8: the oracle on three projections
+    st = synth.workload("ell128").subset([0, 57, 131])
+    ph = synth.phantom("ell128")
+    c = (0.6 * oracle.zonal_to_sh(st.ell_max, ph.dirs.reshape(-1, 3), ph.amps.reshape(-1, st.ell_max // 2 + 1))
+         ).reshape(st.volume_shape).astype(np.float32)
+    g_or = geom(st)
+    I = (oracle.forward(g_or, c.astype(np.float64) / 0.6) + 1.0).astype(np.float32)
+    t0 = time.perf_counter()
+    L_ref, g_ref = oracle.gradient_residual(g_or, c.astype(np.float64), I.astype(np.float64))
+    t_or = time.perf_counter() - t0
+    row = {"oracle_s_per_eval_3_projections": t_or, "oracle_cores": 1,
+           "inputs": "projections 0, 57, 131; 0.6 x the 12-ellipsoid phantom, data its projection + 1",
+           "tolerance": {"f32": 1e-5, "bf16": 5e-3, "f16": 1e-3}}
+    for prec in ("f32", "bf16", "f16"):
+        h = tt.Handle(st, prec)
+        L, g = h.gradient_residual(torch.as_tensor(c, device="cuda"), torch.as_tensor(I, device="cuda"))
+        row[prec] = {"loss_rel_err": abs(L - L_ref) / abs(L_ref), "grad_rel_l2": rel(g.cpu().numpy(), g_ref)}
+        h.close()
+    out["ell128_precision"] = row
     return out
 
 
